@@ -1,0 +1,207 @@
+/*
+ * xeb.h -- C ABI of the GB300 multi-amplitude contraction library.
+ *
+ * The library computes the amplitudes <s_i|C|0^n> of a quantum circuit C for
+ * a set of k bitstrings s_1..s_k by evaluating ONE contraction tree T of the
+ * circuit's tensor network on k leaf assignments (Sec. "Multi-batch
+ * simulator"), where every subtree T' is contracted once per distinct value
+ * of the output bits it depends on (the memoization of Sec. "Multi-tensor
+ * contraction algorithm", Fig. "main idea", Alg. 1-4).  Legs may be sliced
+ * (App. A, "Slicing"): the contraction runs once per value of the sliced legs
+ * and the results are summed in FP64.  The squared moduli are then folded
+ * into the linear XEB F = 2^n/k sum_i |<s_i|C|0^n>|^2 - 1 (Eq. 1).
+ *
+ * General rules
+ *  - Every function returns an xeb_status; nothing throws across the ABI.
+ *    On a non-OK status xeb_last_error() returns a thread-local message.
+ *  - The caller owns every array it passes in; the library copies what it
+ *    keeps.  Pointers documented as "device" must be CUDA device pointers
+ *    of the current device; "host" pointers are ordinary host memory.
+ *  - Work is enqueued on the CUDA stream the caller passes (cudaStream_t cast
+ *    to uintptr_t; 0 = legacy default stream).  Functions that return host
+ *    results synchronise that stream.
+ *  - Bitstrings: bit q of a uint64 word is qubit q's measured value (n <= 64).
+ *  - Complex numbers are interleaved (re, im) pairs.
+ *
+ * Tensor-network convention (interface shared by every user of the tree and
+ * slice formats):
+ *  - one leaf per 2-qubit gate, numbered in time order;
+ *  - a 1-qubit gate on q is fused into the output side of the latest 2-qubit
+ *    gate on q before it; 1-qubit gates before the first 2-qubit gate on q
+ *    act on |0> and that vector is contracted into the first 2-qubit gate's
+ *    input for q;  a qubit without 2-qubit gates gets a rank-1 leaf appended
+ *    after the gate leaves (qubit order);
+ *  - bond legs are numbered in the order they are closed: at a 2-qubit gate
+ *    on (qa, qb), first qa's incoming wire (if any), then qb's;
+ *  - the open (output) leg of qubit q sits on the last leaf touching q; a leaf
+ *    with two open legs lists them in its gate's qubit order.
+ *  - Trees are lists of (left, right) pairs in post-order; a child c >= 0 is an
+ *    earlier pair, c < 0 is leaf -1-c; the last pair is the root.
+ *  - Output bits are ordered by an in-order walk of the tree (pi); a node's
+ *    bits form a contiguous range of pi, read as a binary number with pi's
+ *    first bit most significant; key ids are ranks of the distinct values in
+ *    ascending order (App. C: variables numbered by position, lexicographic
+ *    order of the index tuples).
+ */
+#ifndef XEB_H_
+#define XEB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    XEB_OK = 0,
+    XEB_EINVAL = 1,        /* invalid argument (message says which)            */
+    XEB_ENOMEM = 2,        /* device or host allocation failed / too small     */
+    XEB_ECUDA = 3,         /* a CUDA runtime call failed                       */
+    XEB_ETIMEOUT = 4,      /* a device-side bounded wait gave up               */
+    XEB_EUNSUPPORTED = 5,  /* valid request this build does not support        */
+    XEB_ECANCELLED = 6,
+    XEB_EDEVICE = 7        /* a device-side consistency check failed           */
+} xeb_status;
+
+/* Arithmetic of the pairwise contractions (Eq. elem-cont). */
+enum {
+    XEB_PREC_FP32 = 0,     /* plain FP32 complex FMA on CUDA cores             */
+    XEB_PREC_TF32X3 = 1,   /* tcgen05 kind::tf32, 3-term split, FP32 accumulate */
+    XEB_PREC_FP64 = 2      /* FP64 complex FMA on CUDA cores (checks)          */
+};
+
+/* Planner strategies (App. A objective f(T) picks among candidates). */
+enum {
+    XEB_PLANNER_AUTO = 0,
+    XEB_PLANNER_GREEDY = 1,  /* memo-aware greedy pairwise merging             */
+    XEB_PLANNER_SWEEP = 2    /* time-ordered body of gate blocks + output trie */
+};
+
+typedef struct {
+    int n_qubits;
+    int n_gates;
+    const int32_t* kinds;  /* host [n_gates]: 1 = one-qubit gate, 2 = two-qubit */
+    const int32_t* q0;     /* host [n_gates]                                     */
+    const int32_t* q1;     /* host [n_gates]; ignored for one-qubit gates        */
+    const double* mats;    /* host [n_gates][4][4] complex, row-major; a 2x2 gate
+                              uses the top-left block; a 4x4 gate on (qa, qb) is
+                              in the basis |b_a b_b> (qa's bit high)             */
+} xeb_circuit;
+
+typedef struct {
+    int n_nodes;              /* = number of leaves - 1                          */
+    const int32_t* children;  /* host [2*n_nodes], see the tree convention       */
+} xeb_tree;
+
+typedef struct {
+    int n;                    /* number of sliced bond legs                      */
+    const int32_t* legs;      /* host [n] bond-leg ids                           */
+} xeb_slices;
+
+typedef struct {
+    int precision;        /* XEB_PREC_*                                          */
+    int planner;          /* XEB_PLANNER_*                                       */
+    int block_qubits;     /* sweep planner: max qubits per body block (0 = try)  */
+    int group_leaves;     /* sweep planner: output leaves per trie level (0=try) */
+    double alpha;         /* objective: arithmetic intensity (0 = from precision) */
+    double beta;          /* objective: memory penalty factor                    */
+    uint64_t mem_budget;  /* M_max in bytes for the contraction arena            */
+    uint64_t seed;        /* planner randomisation                               */
+    int greedy_trials;    /* randomised greedy restarts                          */
+    int reserved[7];
+} xeb_plan_opts;
+
+typedef struct {
+    int n_qubits, n_leaves, n_legs, n_nodes;
+    int n_sliced;
+    uint64_t k;                 /* bitstrings                                    */
+    uint64_t k_distinct;        /* distinct bitstrings (root evaluations)        */
+    double flops_per_slice;     /* 8 * sum_v k_v 2^(q_v + r_v)                    */
+    double single_amp_flops;    /* 8 * k * sum_v 2^(q_v + r_v) (no memoization)  */
+    double rw_elems_per_slice;  /* sum_v k_v (m(L) + m(R) + m(v))                 */
+    double permute_elems_per_slice;  /* elements moved by layout permutations     */
+    double objective;           /* f(T) of App. A                                 */
+    uint64_t arena_bytes;       /* exact peak of the contraction arena (emulated) */
+    uint64_t device_bytes;      /* total device memory the plan needs             */
+    uint64_t n_slices;          /* 2^n_sliced                                     */
+    int n_gemm_ops, n_permute_ops;
+    int planner_used;
+    int reserved[5];
+} xeb_stats;
+
+/* Default options (FP32, AUTO planner, 64 GiB budget). */
+void xeb_default_opts(xeb_plan_opts* opts);
+
+/* Leaf/leg counts of the circuit's tensor network (convention above). */
+xeb_status xeb_network_info(const xeb_circuit* circuit, int* n_leaves, int* n_legs);
+
+/* Per leaf: its output qubits (out_bits[2*j..2*j+1], -1 padded) and bond legs
+ * (legs[4*j..4*j+3], -1 padded).  Host arrays of 2*n_leaves and 4*n_leaves. */
+xeb_status xeb_network_leaves(const xeb_circuit* circuit, int32_t* out_bits, int32_t* legs);
+
+/* Build a plan (host only; touches no GPU).  bitstrings: host [k].  tree and
+ * slices may be NULL, then the planner chooses them by the objective
+ * f(T) = beta*max(log2(M/M_max), 0) + log2(C + alpha*RW) (App. A).  The plan
+ * evaluates exactly these k bitstrings (exact evaluation counts k_v). */
+xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                           const xeb_tree* tree, const xeb_slices* slices,
+                           const xeb_plan_opts* opts, struct xeb_plan_s** out);
+
+void xeb_plan_destroy(struct xeb_plan_s* plan);
+
+/* Statistics of a plan (host only). */
+xeb_status xeb_plan_stats(struct xeb_plan_s* plan, xeb_stats* out);
+
+/* The chosen tree (host [2*(n_leaves-1)]) and slices (host [n_sliced]). */
+xeb_status xeb_plan_tree(struct xeb_plan_s* plan, int32_t* children, int32_t* sliced_legs);
+
+/* Exact evaluation count k_v and pi-range [a, b) of internal node `node`
+ * (host only); counts come from the plan's bitstrings. */
+xeb_status xeb_plan_node(struct xeb_plan_s* plan, int node, int64_t* kv, int32_t* a,
+                         int32_t* b, int32_t* n_legs, int32_t* n_shared);
+
+/* Device memory the plan needs (bytes) for xeb_plan_bind. */
+size_t xeb_plan_device_bytes(struct xeb_plan_s* plan);
+
+/* Attach device memory and upload the plan's constant tables on `stream`.
+ * workspace: device pointer of >= xeb_plan_device_bytes() bytes owned by the
+ * caller (kept until destroy), or NULL to let the library allocate it. */
+xeb_status xeb_plan_bind(struct xeb_plan_s* plan, void* workspace, size_t bytes,
+                         uintptr_t stream);
+
+/* Memo key tables (a1, on the device): read `k` bitstrings from device memory
+ * (must equal the plan's k and give the plan's counts; a mismatch returns
+ * XEB_EDEVICE) and build, for every node, the key id of each bitstring and
+ * the children's key ids (uL, uR) of each key. */
+xeb_status xeb_set_bitstrings(struct xeb_plan_s* plan, const uint64_t* bitstrings_dev,
+                              size_t k, uintptr_t stream);
+
+/* Contract every slice (a2..a6) and write the k amplitudes, in input order,
+ * as complex128 to device memory out_dev [2*k doubles]. */
+xeb_status xeb_amplitudes(struct xeb_plan_s* plan, double* out_dev, uintptr_t stream);
+
+/* Linear XEB of the last xeb_amplitudes call (Eq. 1): F, mean of 2^n p and
+ * mean of (2^n p)^2 over the sequence; host outputs; synchronises. */
+xeb_status xeb_fidelity(struct xeb_plan_s* plan, double* F, double* mean_2np,
+                        double* mean_2np_sq, uintptr_t stream);
+
+/* End to end from host memory: copy bitstrings_host [k] (pinned for async
+ * speed) to the device, build key tables, contract, copy amplitudes
+ * [2*k doubles] and F to host.  Synchronises. */
+xeb_status xeb_run(struct xeb_plan_s* plan, const uint64_t* bitstrings_host, size_t k,
+                   double* amps_host, double* F_host, uintptr_t stream);
+
+/* Copy node `node`'s device key tables to host (for checks): key_of_bitstring
+ * [k] int32, uL [k_v], uR [k_v] int32 (any may be NULL).  Synchronises. */
+xeb_status xeb_plan_keys(struct xeb_plan_s* plan, int node, int32_t* key_of_bitstring,
+                         int32_t* uL, int32_t* uR, uintptr_t stream);
+
+/* Thread-local message of the last failure in this thread. */
+const char* xeb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XEB_H_ */

@@ -1,0 +1,285 @@
+"""ctypes binding of the C ABI in include/xeb.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  The library
+must have been built (``paper_2108_05665_gb300.build.build()``); loading fails
+loudly otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+XEB_OK = 0
+STATUS_NAMES = {0: "XEB_OK", 1: "XEB_EINVAL", 2: "XEB_ENOMEM", 3: "XEB_ECUDA", 4: "XEB_ETIMEOUT",
+                5: "XEB_EUNSUPPORTED", 6: "XEB_ECANCELLED", 7: "XEB_EDEVICE"}
+
+XEB_PREC_FP32 = 0
+XEB_PREC_TF32X3 = 1
+XEB_PREC_FP64 = 2
+
+XEB_PLANNER_AUTO = 0
+XEB_PLANNER_GREEDY = 1
+XEB_PLANNER_SWEEP = 2
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_dblp = ctypes.POINTER(ctypes.c_double)
+
+
+class XebError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class xeb_circuit(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("n_gates", ctypes.c_int), ("kinds", _i32p),
+                ("q0", _i32p), ("q1", _i32p), ("mats", _dblp)]
+
+
+class xeb_tree(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int), ("children", _i32p)]
+
+
+class xeb_slices(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("legs", _i32p)]
+
+
+class xeb_plan_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("planner", ctypes.c_int), ("block_qubits", ctypes.c_int),
+                ("group_leaves", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("mem_budget", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("greedy_trials", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class xeb_stats(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("n_leaves", ctypes.c_int), ("n_legs", ctypes.c_int),
+                ("n_nodes", ctypes.c_int), ("n_sliced", ctypes.c_int), ("k", ctypes.c_uint64),
+                ("k_distinct", ctypes.c_uint64), ("flops_per_slice", ctypes.c_double),
+                ("single_amp_flops", ctypes.c_double), ("rw_elems_per_slice", ctypes.c_double),
+                ("permute_elems_per_slice", ctypes.c_double), ("objective", ctypes.c_double),
+                ("arena_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("n_slices", ctypes.c_uint64), ("n_gemm_ops", ctypes.c_int), ("n_permute_ops", ctypes.c_int),
+                ("planner_used", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
+
+
+_PROTOS = {
+    "xeb_default_opts": (None, [ctypes.POINTER(xeb_plan_opts)]),
+    "xeb_network_info": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "xeb_network_leaves": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _i32p, _i32p]),
+    "xeb_plan_create": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _u64p, ctypes.c_size_t,
+                                       ctypes.POINTER(xeb_tree), ctypes.POINTER(xeb_slices),
+                                       ctypes.POINTER(xeb_plan_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "xeb_plan_destroy": (None, [ctypes.c_void_p]),
+    "xeb_plan_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(xeb_stats)]),
+    "xeb_plan_tree": (ctypes.c_int, [ctypes.c_void_p, _i32p, _i32p]),
+    "xeb_plan_node": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i64p, _i32p, _i32p, _i32p, _i32p]),
+    "xeb_plan_device_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "xeb_plan_bind": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "xeb_set_bitstrings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "xeb_amplitudes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "xeb_fidelity": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp, _dblp, ctypes.c_void_p]),
+    "xeb_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, _dblp,
+                               ctypes.c_void_p]),
+    "xeb_plan_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_void_p]),
+    "xeb_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libxeb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = path or _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("native library %s is missing: run paper_2108_05665_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != XEB_OK:
+        raise XebError(status, load().xeb_last_error().decode())
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+class CircuitArrays:
+    """Keeps the numpy arrays behind an xeb_circuit alive."""
+
+    def __init__(self, circuit):
+        kinds, q0, q1, mats = circuit.as_arrays()
+        self.kinds = np.ascontiguousarray(kinds, dtype=np.int32)
+        self.q0 = np.ascontiguousarray(q0, dtype=np.int32)
+        self.q1 = np.ascontiguousarray(q1, dtype=np.int32)
+        self.mats = np.ascontiguousarray(mats, dtype=np.complex128).view(np.float64)
+        self.c = xeb_circuit(circuit.n_qubits, len(self.kinds), _ptr(self.kinds, ctypes.c_int32),
+                             _ptr(self.q0, ctypes.c_int32), _ptr(self.q1, ctypes.c_int32),
+                             _ptr(self.mats, ctypes.c_double))
+
+
+def xeb_default_opts() -> xeb_plan_opts:
+    o = xeb_plan_opts()
+    load().xeb_default_opts(ctypes.byref(o))
+    return o
+
+
+def xeb_network_info(circuit):
+    ca = CircuitArrays(circuit)
+    nl, ng = ctypes.c_int(), ctypes.c_int()
+    _check(load().xeb_network_info(ctypes.byref(ca.c), ctypes.byref(nl), ctypes.byref(ng)))
+    return nl.value, ng.value
+
+
+def xeb_network_leaves(circuit):
+    nl, _ = xeb_network_info(circuit)
+    ca = CircuitArrays(circuit)
+    out = np.empty(2 * nl, dtype=np.int32)
+    legs = np.empty(4 * nl, dtype=np.int32)
+    _check(load().xeb_network_leaves(ctypes.byref(ca.c), _ptr(out, ctypes.c_int32), _ptr(legs, ctypes.c_int32)))
+    return ([list(x[x >= 0]) for x in out.reshape(-1, 2)], [list(x[x >= 0]) for x in legs.reshape(-1, 4)])
+
+
+def xeb_plan_create(circuit, bitstrings, tree: Optional[Sequence] = None, slices: Optional[Sequence[int]] = None,
+                    opts: Optional[xeb_plan_opts] = None) -> ctypes.c_void_p:
+    ca = CircuitArrays(circuit)
+    bs = np.ascontiguousarray(bitstrings, dtype=np.uint64)
+    tp = None
+    if tree is not None:
+        ch = np.ascontiguousarray(np.asarray(tree, dtype=np.int32).reshape(-1))
+        t = xeb_tree(len(ch) // 2, _ptr(ch, ctypes.c_int32))
+        tp = ctypes.byref(t)
+    sp = None
+    if slices is not None:
+        sl = np.ascontiguousarray(np.asarray(slices, dtype=np.int32))
+        s = xeb_slices(len(sl), _ptr(sl, ctypes.c_int32))
+        sp = ctypes.byref(s)
+    out = ctypes.c_void_p()
+    _check(load().xeb_plan_create(ctypes.byref(ca.c), _ptr(bs, ctypes.c_uint64), len(bs), tp, sp,
+                                  ctypes.byref(opts) if opts is not None else None, ctypes.byref(out)))
+    return out
+
+
+def xeb_plan_destroy(plan):
+    load().xeb_plan_destroy(plan)
+
+
+def xeb_plan_stats(plan) -> dict:
+    s = xeb_stats()
+    _check(load().xeb_plan_stats(plan, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def xeb_plan_tree(plan):
+    st = xeb_plan_stats(plan)
+    ch = np.empty(2 * st["n_nodes"], dtype=np.int32)
+    sl = np.empty(max(st["n_sliced"], 1), dtype=np.int32)
+    _check(load().xeb_plan_tree(plan, _ptr(ch, ctypes.c_int32), _ptr(sl, ctypes.c_int32)))
+    return [tuple(int(x) for x in p) for p in ch.reshape(-1, 2)], [int(x) for x in sl[: st["n_sliced"]]]
+
+
+def xeb_plan_node(plan, node: int):
+    kv = ctypes.c_int64()
+    a, b, nl, ns = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().xeb_plan_node(plan, node, ctypes.byref(kv), ctypes.byref(a), ctypes.byref(b),
+                                ctypes.byref(nl), ctypes.byref(ns)))
+    return {"kv": kv.value, "a": a.value, "b": b.value, "n_legs": nl.value, "n_shared": ns.value}
+
+
+def xeb_plan_device_bytes(plan) -> int:
+    return int(load().xeb_plan_device_bytes(plan))
+
+
+def xeb_plan_bind(plan, workspace_ptr: int, nbytes: int, stream: int):
+    _check(load().xeb_plan_bind(plan, ctypes.c_void_p(workspace_ptr or None), nbytes, ctypes.c_void_p(stream or None)))
+
+
+def xeb_set_bitstrings(plan, bits_dev_ptr: int, k: int, stream: int):
+    _check(load().xeb_set_bitstrings(plan, ctypes.c_void_p(bits_dev_ptr), k, ctypes.c_void_p(stream or None)))
+
+
+def xeb_amplitudes(plan, out_dev_ptr: int, stream: int):
+    _check(load().xeb_amplitudes(plan, ctypes.c_void_p(out_dev_ptr or None), ctypes.c_void_p(stream or None)))
+
+
+def xeb_fidelity(plan, stream: int):
+    F, m1, m2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().xeb_fidelity(plan, ctypes.byref(F), ctypes.byref(m1), ctypes.byref(m2),
+                               ctypes.c_void_p(stream or None)))
+    return F.value, m1.value, m2.value
+
+
+def xeb_run(plan, bits_host_ptr: int, k: int, amps_host_ptr: int, stream: int) -> float:
+    F = ctypes.c_double()
+    _check(load().xeb_run(plan, ctypes.c_void_p(bits_host_ptr), k, ctypes.c_void_p(amps_host_ptr or None),
+                          ctypes.byref(F), ctypes.c_void_p(stream or None)))
+    return F.value
+
+
+def xeb_plan_keys(plan, node: int, k: int, kv: int, stream: int):
+    key = np.empty(k, dtype=np.int32)
+    uL = np.empty(max(kv, 1), dtype=np.int32)
+    uR = np.empty(max(kv, 1), dtype=np.int32)
+    _check(load().xeb_plan_keys(plan, node, _ptr(key, ctypes.c_int32), _ptr(uL, ctypes.c_int32),
+                                _ptr(uR, ctypes.c_int32), ctypes.c_void_p(stream or None)))
+    return key, uL[:kv], uR[:kv]
+
+
+class Plan:
+    """Owner of one xeb_plan handle plus the torch buffers it is bound to."""
+
+    def __init__(self, circuit, bitstrings, tree=None, slices=None, opts=None):
+        self.handle = xeb_plan_create(circuit, bitstrings, tree, slices, opts)
+        self.k = len(bitstrings)
+        self.n = circuit.n_qubits
+        self.workspace = None
+
+    def stats(self):
+        return xeb_plan_stats(self.handle)
+
+    def tree(self):
+        return xeb_plan_tree(self.handle)
+
+    def bind(self, device="cuda"):
+        import torch
+        nbytes = xeb_plan_device_bytes(self.handle)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        ptr = self.workspace.data_ptr()
+        ptr = (ptr + 255) // 256 * 256
+        xeb_plan_bind(self.handle, ptr, nbytes, torch.cuda.current_stream().cuda_stream)
+        return self
+
+    def close(self):
+        if self.handle is not None:
+            xeb_plan_destroy(self.handle)
+            self.handle = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,771 @@
+// C ABI (include/xeb.h): planning, device layout of a plan, and the driver
+// that enqueues the kernels of kernels.cu in tree order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "plan.h"
+#include "xeb.h"
+
+using namespace xebp;
+
+namespace {
+thread_local std::string g_err;
+
+xeb_status fail(xeb_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define XEB_CUDA(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(XEB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct GemmLaunch {
+    int kernel;
+    xebk::GemmDesc d;
+};
+}  // namespace
+
+struct xeb_plan_s {
+    Network net;
+    Tree tree;
+    std::vector<int> sliced;
+    Analysis an;
+    Program prog;
+    Costs costs;
+    double objective = 0;
+    int planner_used = 0;
+    xeb_plan_opts opts{};
+    std::vector<uint64_t> bits;
+    size_t k = 0;
+    size_t elem = 8;
+    // device state
+    bool bound = false;
+    bool owns = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t off_arena = 0, off_leafdata = 0, off_tables = 0;
+    size_t bytes_total = 0;
+    // offsets inside tables (bytes)
+    int64_t t_trie_desc = 0, t_internal = 0, t_leaf_desc = 0, t_pi = 0, t_bits = 0, t_acc = 0, t_amps = 0,
+            t_partials = 0, t_result = 0, t_err = 0;
+    int64_t tables_bytes = 0;
+    std::vector<xebk::TrieDesc> trie;
+    std::vector<int> trie_of_node;  // node -> index in trie, -1 if no bits
+    std::vector<int> trie_internal;
+    std::vector<xebk::LeafDesc> leafdesc;
+    std::vector<int64_t> leaf_src_off;
+    int64_t leafdata_elems = 0;
+    std::vector<xebk::PermDesc> perms;  // per op (unused for GEMM)
+    std::vector<GemmLaunch> gemms;      // per op (unused for PERM)
+    int max_kv = 1;
+    int n_xeb_blocks = 64;
+    bool tables_ready = false;
+    bool amps_ready = false;
+};
+
+extern "C" {
+
+const char* xeb_last_error(void) { return g_err.c_str(); }
+
+void xeb_default_opts(xeb_plan_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = XEB_PREC_FP32;
+    o->planner = XEB_PLANNER_AUTO;
+    o->beta = 10.0;
+    o->mem_budget = uint64_t(64) << 30;
+    o->seed = 1;
+    o->greedy_trials = 4;
+}
+
+xeb_status xeb_network_info(const xeb_circuit* c, int* n_leaves, int* n_legs) {
+    Network net;
+    std::string err;
+    if (!build_network(c, net, err)) return fail(XEB_EINVAL, err);
+    if (n_leaves) *n_leaves = int(net.leaves.size());
+    if (n_legs) *n_legs = net.n_legs;
+    return XEB_OK;
+}
+
+xeb_status xeb_network_leaves(const xeb_circuit* c, int32_t* out_bits, int32_t* legs) {
+    Network net;
+    std::string err;
+    if (!build_network(c, net, err)) return fail(XEB_EINVAL, err);
+    for (size_t j = 0; j < net.leaves.size(); ++j) {
+        const Leaf& lf = net.leaves[j];
+        if (out_bits)
+            for (int t = 0; t < 2; ++t) out_bits[2 * j + t] = t < int(lf.out_q.size()) ? lf.out_q[t] : -1;
+        if (legs)
+            for (int t = 0; t < 4; ++t) legs[4 * j + t] = t < int(lf.legs.size()) ? lf.legs[t] : -1;
+    }
+    return XEB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+double default_alpha(int prec) {
+    // complex multiply-adds per element moved at which compute and HBM time
+    // balance on GB300 (FP32 CUDA cores ~10 T cMAC/s, 3xTF32 tensor cores
+    // ~40 T cMAC/s, HBM ~0.84 T complex64 elements/s)
+    switch (prec) {
+        case XEB_PREC_TF32X3: return 48.0;
+        case XEB_PREC_FP64: return 1.0;
+        default: return 12.0;
+    }
+}
+
+struct Candidate {
+    Tree tree;
+    Analysis an;
+    Program prog;
+    Costs costs;
+    double f = 0;
+    int64_t arena_bytes = 0;
+};
+
+bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& sliced, DistinctCounter& dc,
+              const xeb_plan_opts& o, size_t elem, uint64_t k, Candidate& cand, std::string& err) {
+    cand.tree = tree;
+    if (!analyze(net, tree, sliced, cand.an, err)) return false;
+    fill_counts(cand.an, dc);
+    build_program(cand.an, cand.prog);
+    plan_memory(cand.prog);
+    cand.costs = tree_costs(cand.an, cand.prog, k);
+    cand.arena_bytes = cand.prog.arena_elems * int64_t(elem);
+    const double alpha = o.alpha > 0 ? o.alpha : default_alpha(o.precision);
+    const double budget = double(std::max<uint64_t>(o.mem_budget, 1));
+    const double nsl = std::ldexp(1.0, int(sliced.size()));
+    cand.f = o.beta * std::max(std::log2(double(cand.arena_bytes) / budget), 0.0) +
+             std::log2(nsl * (cand.costs.C + alpha * (cand.costs.RW + cand.costs.perm)) + 1.0);
+    return true;
+}
+
+}  // namespace
+
+extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                                      const xeb_tree* tree, const xeb_slices* slices,
+                                      const xeb_plan_opts* opts, xeb_plan_s** out) {
+    if (!out) return fail(XEB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (k == 0 || !bitstrings) return fail(XEB_EINVAL, "need k >= 1 bitstrings");
+    if (k > size_t(xebk::kMaxTrieK))
+        return fail(XEB_EUNSUPPORTED, "k > " + std::to_string(xebk::kMaxTrieK) + " bitstrings per plan");
+    std::unique_ptr<xeb_plan_s> p(new xeb_plan_s());
+    if (opts) p->opts = *opts;
+    else xeb_default_opts(&p->opts);
+    const xeb_plan_opts& o = p->opts;
+    if (o.precision != XEB_PREC_FP32 && o.precision != XEB_PREC_FP64 && o.precision != XEB_PREC_TF32X3)
+        return fail(XEB_EINVAL, "unknown precision");
+    p->elem = o.precision == XEB_PREC_FP64 ? 16 : 8;
+    std::string err;
+    if (!build_network(circuit, p->net, err)) return fail(XEB_EINVAL, err);
+    const int n = p->net.n;
+    for (size_t i = 0; i < k; ++i)
+        if (n < 64 && (bitstrings[i] >> n) != 0) return fail(XEB_EINVAL, "bitstring has bits above n");
+    p->bits.assign(bitstrings, bitstrings + k);
+    p->k = k;
+    DistinctCounter dc;
+    dc.bs = p->bits.data();
+    dc.k = k;
+    if (slices && slices->n > 0) {
+        if (!slices->legs) return fail(XEB_EINVAL, "slices->legs is NULL");
+        p->sliced.assign(slices->legs, slices->legs + slices->n);
+        if (p->sliced.size() > 30) return fail(XEB_EUNSUPPORTED, "more than 30 sliced legs");
+    }
+    Candidate best;
+    bool have = false;
+    if (tree) {
+        if (!tree->children && tree->n_nodes > 0) return fail(XEB_EINVAL, "tree->children is NULL");
+        Tree t(tree->n_nodes);
+        for (int i = 0; i < tree->n_nodes; ++i) t[i] = {tree->children[2 * i], tree->children[2 * i + 1]};
+        if (!evaluate(p->net, t, p->sliced, dc, o, p->elem, k, best, err)) return fail(XEB_EINVAL, err);
+        have = true;
+        p->planner_used = 0;
+    } else {
+        if (p->net.leaves.size() < 2) return fail(XEB_EUNSUPPORTED, "network with fewer than two leaves");
+        std::vector<std::pair<int, Tree>> cands;
+        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_GREEDY) {
+            const int trials = std::max(1, o.greedy_trials);
+            for (int t = 0; t < trials; ++t)
+                cands.push_back({XEB_PLANNER_GREEDY, greedy_tree(p->net, dc, p->sliced, o.seed + t, t == 0 ? 0.0 : 0.15)});
+        }
+        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_SWEEP) {
+            std::vector<int> bs, gs;
+            if (o.block_qubits > 0) bs = {o.block_qubits};
+            else for (int b = 2; b <= 10; ++b) bs.push_back(b);
+            if (o.group_leaves > 0) gs = {o.group_leaves};
+            else gs = {1, 2, 3, 4};
+            for (int b : bs)
+                for (int g : gs) {
+                    Tree t;
+                    if (sweep_tree(p->net, b, g, t)) cands.push_back({XEB_PLANNER_SWEEP, t});
+                }
+        }
+        for (auto& c : cands) {
+            Candidate cd_;
+            if (!evaluate(p->net, c.second, p->sliced, dc, o, p->elem, k, cd_, err)) continue;
+            if (!have || cd_.f < best.f) {
+                best = std::move(cd_);
+                have = true;
+                p->planner_used = c.first;
+            }
+        }
+        if (!have) return fail(XEB_EINVAL, "planner found no valid tree: " + err);
+    }
+    // slicing (App. A, "Slicing"): add the leg with the best memory reduction
+    // until the arena fits the budget
+    if (!slices) {
+        while (uint64_t(best.arena_bytes) > o.mem_budget && p->sliced.size() < 30) {
+            std::vector<int> order(best.an.nodes.size());
+            for (size_t v = 0; v < order.size(); ++v) order[v] = int(v);
+            std::sort(order.begin(), order.end(), [&](int x, int y) {
+                const double ex = double(best.an.nodes[x].kv) * std::ldexp(1.0, int(best.an.nodes[x].legs.size()));
+                const double ey = double(best.an.nodes[y].kv) * std::ldexp(1.0, int(best.an.nodes[y].legs.size()));
+                return ex > ey;
+            });
+            std::vector<int> legs;
+            for (int t = 0; t < std::min<int>(3, int(order.size())); ++t)
+                for (int l : best.an.nodes[order[t]].legs)
+                    if (std::find(legs.begin(), legs.end(), l) == legs.end()) legs.push_back(l);
+            Candidate bc;
+            int bl = -1;
+            for (int l : legs) {
+                std::vector<int> s2 = p->sliced;
+                s2.push_back(l);
+                Candidate c;
+                if (!evaluate(p->net, best.tree, s2, dc, o, p->elem, k, c, err)) continue;
+                if (bl < 0 || c.arena_bytes < bc.arena_bytes) {
+                    bc = std::move(c);
+                    bl = l;
+                }
+            }
+            if (bl < 0 || bc.arena_bytes >= best.arena_bytes) break;
+            p->sliced.push_back(bl);
+            best = std::move(bc);
+        }
+    }
+    p->tree = best.tree;
+    p->an = std::move(best.an);
+    p->prog = std::move(best.prog);
+    p->costs = best.costs;
+    p->objective = best.f;
+    *out = p.release();
+    return XEB_OK;
+}
+
+extern "C" void xeb_plan_destroy(xeb_plan_s* p) {
+    if (!p) return;
+    if (p->owns && p->ws) cudaFree(p->ws);
+    delete p;
+}
+
+extern "C" xeb_status xeb_plan_stats(xeb_plan_s* p, xeb_stats* s) {
+    if (!p || !s) return fail(XEB_EINVAL, "NULL argument");
+    std::memset(s, 0, sizeof(*s));
+    s->n_qubits = p->net.n;
+    s->n_leaves = int(p->net.leaves.size());
+    s->n_legs = p->net.n_legs;
+    s->n_nodes = int(p->tree.size());
+    s->n_sliced = int(p->sliced.size());
+    s->k = p->k;
+    s->k_distinct = uint64_t(p->an.nodes.back().kv);
+    s->flops_per_slice = 8.0 * p->costs.C;
+    s->single_amp_flops = 8.0 * p->costs.single;
+    s->rw_elems_per_slice = p->costs.RW;
+    s->permute_elems_per_slice = p->costs.perm;
+    s->objective = p->objective;
+    s->arena_bytes = uint64_t(p->prog.arena_elems) * p->elem;
+    s->device_bytes = xeb_plan_device_bytes(p);
+    s->n_slices = uint64_t(1) << p->sliced.size();
+    for (const Op& op : p->prog.ops) {
+        if (op.kind == OP_GEMM) ++s->n_gemm_ops;
+        else ++s->n_permute_ops;
+    }
+    s->planner_used = p->planner_used;
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_tree(xeb_plan_s* p, int32_t* children, int32_t* sliced_legs) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    if (children)
+        for (size_t i = 0; i < p->tree.size(); ++i) {
+            children[2 * i] = p->tree[i][0];
+            children[2 * i + 1] = p->tree[i][1];
+        }
+    if (sliced_legs)
+        for (size_t i = 0; i < p->sliced.size(); ++i) sliced_legs[i] = p->sliced[i];
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_node(xeb_plan_s* p, int node, int64_t* kv, int32_t* a, int32_t* b, int32_t* n_legs,
+                                    int32_t* n_shared) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    if (node < 0 || node >= int(p->tree.size())) return fail(XEB_EINVAL, "node out of range");
+    const Node& nd = p->an.nodes[p->an.L + node];
+    if (kv) *kv = nd.kv;
+    if (a) *a = nd.a;
+    if (b) *b = nd.b;
+    if (n_legs) *n_legs = int32_t(nd.legs.size());
+    if (n_shared) *n_shared = nd.q;
+    return XEB_OK;
+}
+
+namespace {
+
+// Device layout of a plan: [arena][leaf data][tables].
+void layout_device(xeb_plan_s* p) {
+    const Analysis& an = p->an;
+    const int N = int(an.nodes.size());
+    const int L = an.L;
+    const int64_t A = 256;
+    int64_t off = 0;
+    p->off_arena = 0;
+    off = align_up(p->prog.arena_elems * int64_t(p->elem), A);
+    p->off_leafdata = off;
+    p->leaf_src_off.assign(L, 0);
+    int64_t le = 0;
+    for (int j = 0; j < L; ++j) {
+        p->leaf_src_off[j] = le;
+        const Leaf& lf = p->net.leaves[j];
+        le += int64_t(1) << (lf.out_q.size() + lf.legs.size());
+    }
+    p->leafdata_elems = le;
+    off = align_up(off + le * int64_t(p->elem), A);
+    p->off_tables = off;
+    // tables
+    int64_t t = 0;
+    auto take = [&](int64_t bytes) {
+        const int64_t r = t;
+        t = align_up(t + std::max<int64_t>(bytes, 1), A);
+        return r;
+    };
+    p->trie.clear();
+    p->trie_of_node.assign(N, -1);
+    p->trie_internal.clear();
+    p->max_kv = 1;
+    for (int v = 0; v < N; ++v)
+        if (an.nodes[v].b > an.nodes[v].a) {
+            p->trie_of_node[v] = int(p->trie.size());
+            xebk::TrieDesc d{};
+            d.a = an.nodes[v].a;
+            d.b = an.nodes[v].b;
+            d.kv = int(an.nodes[v].kv);
+            d.is_internal = v >= L;
+            p->trie.push_back(d);
+            p->max_kv = std::max(p->max_kv, d.kv);
+        }
+    p->t_trie_desc = take(int64_t(p->trie.size()) * int64_t(sizeof(xebk::TrieDesc)));
+    p->t_internal = take(int64_t(p->trie.size()) * 4);
+    p->t_leaf_desc = take(int64_t(L) * int64_t(sizeof(xebk::LeafDesc)));
+    p->t_pi = take(int64_t(p->net.n) * 4);
+    p->t_bits = take(int64_t(p->k) * 8);
+    for (int v = 0; v < N; ++v) {
+        const int ti = p->trie_of_node[v];
+        if (ti < 0) continue;
+        xebk::TrieDesc& d = p->trie[ti];
+        d.key_off = take(int64_t(p->k) * 4);
+        d.uniq_off = take(int64_t(d.kv) * 8);
+        d.rep_off = take(int64_t(d.kv) * 4);
+        d.uL_off = d.uR_off = d.gstart_off = -1;
+        d.l_key_off = d.r_key_off = -1;
+        if (v >= L) {
+            d.uL_off = take(int64_t(d.kv) * 4);
+            d.uR_off = take(int64_t(d.kv) * 4);
+            d.kL = int(an.nodes[an.nodes[v].l].kv);
+            d.gstart_off = take(int64_t(d.kL + 1) * 4);
+        }
+    }
+    for (int v = L; v < N; ++v) {
+        const int ti = p->trie_of_node[v];
+        if (ti < 0) continue;
+        xebk::TrieDesc& d = p->trie[ti];
+        const int tl = p->trie_of_node[an.nodes[v].l], tr = p->trie_of_node[an.nodes[v].r];
+        d.l_key_off = tl >= 0 ? p->trie[tl].key_off : -1;
+        d.r_key_off = tr >= 0 ? p->trie[tr].key_off : -1;
+        p->trie_internal.push_back(ti);
+    }
+    p->t_acc = take(an.nodes[N - 1].kv * 16);
+    p->t_amps = take(int64_t(p->k) * 16);
+    p->t_partials = take(int64_t(p->n_xeb_blocks) * 16);
+    p->t_result = take(64);
+    p->t_err = take(16);
+    p->tables_bytes = t;
+    p->bytes_total = size_t(off + t);
+}
+
+std::vector<char> leaf_host_data(xeb_plan_s* p) {
+    std::vector<char> h(size_t(p->leafdata_elems) * p->elem);
+    for (size_t j = 0; j < p->net.leaves.size(); ++j) {
+        const Leaf& lf = p->net.leaves[j];
+        for (size_t e = 0; e < lf.t.size(); ++e) {
+            const int64_t idx = p->leaf_src_off[j] + int64_t(e);
+            if (p->elem == 8) {
+                float* f = reinterpret_cast<float*>(h.data()) + 2 * idx;
+                f[0] = float(lf.t[e].real());
+                f[1] = float(lf.t[e].imag());
+            } else {
+                double* d = reinterpret_cast<double*>(h.data()) + 2 * idx;
+                d[0] = lf.t[e].real();
+                d[1] = lf.t[e].imag();
+            }
+        }
+    }
+    return h;
+}
+
+void build_launches(xeb_plan_s* p) {
+    const Analysis& an = p->an;
+    const Program& pr = p->prog;
+    const int L = an.L;
+    char* tables = p->ws + p->off_tables;
+    // leaves
+    p->leafdesc.assign(L, xebk::LeafDesc{});
+    for (int j = 0; j < L; ++j) {
+        const Leaf& lf = p->net.leaves[j];
+        xebk::LeafDesc& d = p->leafdesc[j];
+        d.dst_off = pr.bufs[pr.node_buf[j]].off;
+        d.src_off = p->leaf_src_off[j];
+        const std::vector<int>& lay = pr.layout[j];
+        d.r = int(lay.size());
+        d.n_out = int(lf.out_q.size());
+        d.n_canon = d.n_out + int(lf.legs.size());
+        d.kv = int(an.nodes[j].kv);
+        for (int b = 0; b < d.r; ++b) {
+            const int leg = lay[d.r - 1 - b];
+            const int axis = d.n_out + int(std::find(lf.legs.begin(), lf.legs.end(), leg) - lf.legs.begin());
+            d.src_pos[b] = d.n_canon - 1 - axis;
+        }
+        d.n_sl = 0;
+        for (size_t a = 0; a < lf.legs.size(); ++a) {
+            const auto it = std::find(p->sliced.begin(), p->sliced.end(), lf.legs[a]);
+            if (it == p->sliced.end()) continue;
+            d.sl_pos[d.n_sl] = d.n_canon - 1 - (d.n_out + int(a));
+            d.sl_bit[d.n_sl] = int(it - p->sliced.begin());
+            ++d.n_sl;
+        }
+        const int ti = p->trie_of_node[j];
+        d.uniq_off = ti >= 0 ? p->trie[ti].uniq_off : -1;
+    }
+    // ops
+    p->perms.assign(pr.ops.size(), xebk::PermDesc{});
+    p->gemms.assign(pr.ops.size(), GemmLaunch{});
+    for (size_t i = 0; i < pr.ops.size(); ++i) {
+        const Op& op = pr.ops[i];
+        if (op.kind == OP_PERM) {
+            xebk::PermDesc& d = p->perms[i];
+            d.r = op.r;
+            d.keys = op.keys;
+            const int r = op.r;
+            std::vector<int> pinv(r);
+            for (int j = 0; j < r; ++j) pinv[op.perm[j]] = j;
+            const int t0 = std::min(r, 5);
+            std::vector<int> U;
+            for (int j = 0; j < t0; ++j) U.push_back(j);
+            for (int j = 0; j < t0; ++j)
+                if (std::find(U.begin(), U.end(), op.perm[j]) == U.end()) U.push_back(op.perm[j]);
+            for (int j = 0; j < r && int(U.size()) < std::min(r, 8); ++j)
+                if (std::find(U.begin(), U.end(), j) == U.end()) U.push_back(j);
+            d.u = int(U.size());
+            for (int i2 = 0; i2 < d.u; ++i2) d.usrc[i2] = U[i2];
+            std::vector<int> Ud;
+            for (int j = 0; j < t0; ++j) Ud.push_back(j);
+            for (int i2 = 0; i2 < d.u; ++i2) {
+                const int dp = pinv[U[i2]];
+                if (std::find(Ud.begin(), Ud.end(), dp) == Ud.end()) Ud.push_back(dp);
+            }
+            for (int i2 = 0; i2 < d.u; ++i2) {
+                d.udst[i2] = Ud[i2];
+                const int sp = op.perm[Ud[i2]];
+                d.udst_e[i2] = int(std::find(U.begin(), U.end(), sp) - U.begin());
+            }
+            d.n_outer = 0;
+            for (int j = 0; j < r; ++j)
+                if (std::find(U.begin(), U.end(), j) == U.end()) {
+                    d.outer_src[d.n_outer] = j;
+                    d.outer_dst[d.n_outer] = pinv[j];
+                    ++d.n_outer;
+                }
+        } else {
+            GemmLaunch& g = p->gemms[i];
+            xebk::GemmDesc& d = g.d;
+            d.M = op.M;
+            d.N = op.N;
+            d.K = op.K;
+            d.kv = op.kv;
+            d.a_off = pr.bufs[op.a_buf].off;
+            d.b_off = pr.bufs[op.b_buf].off;
+            d.c_off = pr.bufs[op.c_buf].off;
+            d.sa_key = op.sa_key; d.sa_m = op.sa_m; d.sa_k = op.sa_k;
+            d.sb_key = op.sb_key; d.sb_k = op.sb_k; d.sb_n = op.sb_n;
+            d.sc_key = op.sc_key; d.sc_m = op.sc_m; d.sc_n = op.sc_n;
+            const int ti = p->trie_of_node[op.node];
+            if (ti >= 0) {
+                const xebk::TrieDesc& t = p->trie[ti];
+                d.uL = reinterpret_cast<const int32_t*>(tables + t.uL_off);
+                d.uR = reinterpret_cast<const int32_t*>(tables + t.uR_off);
+                d.gstart = reinterpret_cast<const int32_t*>(tables + t.gstart_off);
+                d.n_groups = t.kL;
+            } else {
+                d.uL = d.uR = d.gstart = nullptr;
+                d.n_groups = 1;
+            }
+            if (op.M == 1 && op.N == 1) g.kernel = xebk::GK_TAIL;
+            else if (op.N == 1) g.kernel = xebk::GK_GEMV;
+            else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;
+            else g.kernel = xebk::GK_GENERIC;
+        }
+    }
+}
+
+// Every element a launch can touch must lie inside the buffers it names.
+bool validate_launches(const xeb_plan_s* p, std::string& why) {
+    const Program& pr = p->prog;
+    const Analysis& an = p->an;
+    auto inside = [&](int buf, int64_t lo, int64_t hi) {
+        const Buffer& b = pr.bufs[buf];
+        return lo >= b.off && hi < b.off + b.elems && b.off + b.elems <= pr.arena_elems;
+    };
+    for (size_t i = 0; i < pr.ops.size(); ++i) {
+        const Op& op = pr.ops[i];
+        if (op.kind == OP_PERM) {
+            const xebk::PermDesc& d = p->perms[i];
+            std::vector<int> seen_s(d.r, 0), seen_d(d.r, 0);
+            for (int t = 0; t < d.u; ++t) { ++seen_s[d.usrc[t]]; ++seen_d[d.udst[t]]; }
+            for (int t = 0; t < d.n_outer; ++t) { ++seen_s[d.outer_src[t]]; ++seen_d[d.outer_dst[t]]; }
+            for (int t = 0; t < d.r; ++t)
+                if (seen_s[t] != 1 || seen_d[t] != 1) { why = "permutation bits"; return false; }
+            const int64_t n = d.keys << d.r;
+            if (!inside(op.src_buf, pr.bufs[op.src_buf].off, pr.bufs[op.src_buf].off + n - 1) ||
+                !inside(op.dst_buf, pr.bufs[op.dst_buf].off, pr.bufs[op.dst_buf].off + n - 1)) {
+                why = "permutation buffer";
+                return false;
+            }
+            continue;
+        }
+        const xebk::GemmDesc& g = p->gemms[i].d;
+        const int64_t ka = an.nodes[op.a_node].kv, kb = an.nodes[op.b_node].kv;
+        const int64_t a_hi = g.a_off + (ka - 1) * g.sa_key + (g.M - 1) * g.sa_m + (g.K - 1) * g.sa_k;
+        const int64_t b_hi = g.b_off + (kb - 1) * g.sb_key + (g.K - 1) * g.sb_k + (g.N - 1) * g.sb_n;
+        const int64_t c_hi = g.c_off + (g.kv - 1) * g.sc_key + (g.M - 1) * g.sc_m + (g.N - 1) * g.sc_n;
+        if (!inside(op.a_buf, g.a_off, a_hi) || !inside(op.b_buf, g.b_off, b_hi) || !inside(op.c_buf, g.c_off, c_hi)) {
+            why = "gemm operand of node " + std::to_string(op.node);
+            return false;
+        }
+        if ((ka > 1 || kb > 1) && !g.uL) { why = "gemm without key tables"; return false; }
+    }
+    for (size_t j = 0; j < p->leafdesc.size(); ++j) {
+        const xebk::LeafDesc& d = p->leafdesc[j];
+        if (!inside(pr.node_buf[j], d.dst_off, d.dst_off + (int64_t(d.kv) << d.r) - 1)) { why = "leaf dst"; return false; }
+        if (d.src_off + (int64_t(1) << d.n_canon) > p->leafdata_elems) { why = "leaf src"; return false; }
+        for (int b = 0; b < d.r; ++b)
+            if (d.src_pos[b] < 0 || d.src_pos[b] >= d.n_canon - d.n_out) { why = "leaf layout"; return false; }
+    }
+    return true;
+}
+
+template <typename T>
+xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
+    const Analysis& an = p->an;
+    const Program& pr = p->prog;
+    char* tables = p->ws + p->off_tables;
+    T* arena = reinterpret_cast<T*>(p->ws + p->off_arena);
+    const T* leafdata = reinterpret_cast<const T*>(p->ws + p->off_leafdata);
+    double2* acc = reinterpret_cast<double2*>(tables + p->t_acc);
+    const int64_t kv_root = an.nodes.back().kv;
+    XEB_CUDA(cudaMemsetAsync(acc, 0, size_t(kv_root) * 16, st));
+    const int64_t n_slices = int64_t(1) << p->sliced.size();
+    const auto* ldesc = reinterpret_cast<const xebk::LeafDesc*>(tables + p->t_leaf_desc);
+    for (int64_t s = 0; s < n_slices; ++s) {
+        XEB_CUDA(xebk::launch_leaves<T>(ldesc, an.L, leafdata, arena, tables, s, st));
+        for (size_t i = 0; i < pr.ops.size(); ++i) {
+            const Op& op = pr.ops[i];
+            if (op.kind == OP_PERM) {
+                XEB_CUDA(xebk::launch_permute<T>(p->perms[i], arena + pr.bufs[op.src_buf].off,
+                                                 arena + pr.bufs[op.dst_buf].off, st));
+            } else {
+                XEB_CUDA(xebk::launch_gemm<T>(p->gemms[i].kernel, p->gemms[i].d, arena, st));
+            }
+        }
+        XEB_CUDA(xebk::launch_root_accum<T>(arena + pr.bufs[pr.node_buf.back()].off, acc, kv_root, st));
+    }
+    const int troot = p->trie_of_node[int(an.nodes.size()) - 1];
+    const int32_t* key_root = reinterpret_cast<const int32_t*>(tables + p->trie[troot].key_off);
+    XEB_CUDA(xebk::launch_gather_xeb(acc, key_root, int64_t(p->k), amps_out,
+                                     reinterpret_cast<double*>(tables + p->t_partials), p->n_xeb_blocks,
+                                     reinterpret_cast<double*>(tables + p->t_result), p->net.n, st));
+    return XEB_OK;
+}
+
+xeb_status build_tables(xeb_plan_s* p, cudaStream_t st) {
+    char* tables = p->ws + p->off_tables;
+    const auto* tdesc = reinterpret_cast<const xebk::TrieDesc*>(tables + p->t_trie_desc);
+    XEB_CUDA(xebk::launch_trie_keys(tdesc, int(p->trie.size()), reinterpret_cast<const uint64_t*>(tables + p->t_bits),
+                                    int(p->k), reinterpret_cast<const int32_t*>(tables + p->t_pi), tables,
+                                    reinterpret_cast<int32_t*>(tables + p->t_err), st));
+    XEB_CUDA(xebk::launch_trie_links(tdesc, reinterpret_cast<const int*>(tables + p->t_internal),
+                                     int(p->trie_internal.size()), p->max_kv, tables, st));
+    p->tables_ready = true;
+    return XEB_OK;
+}
+
+xeb_status check_bound(xeb_plan_s* p) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    if (!p->bound) return fail(XEB_EINVAL, "plan not bound to device memory (call xeb_plan_bind)");
+    return XEB_OK;
+}
+
+}  // namespace
+
+extern "C" size_t xeb_plan_device_bytes(xeb_plan_s* p) {
+    if (!p) return 0;
+    if (p->bytes_total == 0) layout_device(p);
+    return p->bytes_total;
+}
+
+extern "C" xeb_status xeb_plan_bind(xeb_plan_s* p, void* workspace, size_t bytes, uintptr_t stream) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    if (p->bound) return fail(XEB_EINVAL, "plan already bound");
+    if (p->opts.precision == XEB_PREC_TF32X3)
+        return fail(XEB_EUNSUPPORTED, "TF32x3 tensor-core contraction not built yet");
+    layout_device(p);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (workspace) {
+        if (bytes < p->bytes_total) return fail(XEB_ENOMEM, "workspace smaller than xeb_plan_device_bytes()");
+        if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(XEB_EINVAL, "workspace must be 256-byte aligned");
+        p->ws = static_cast<char*>(workspace);
+        p->owns = false;
+    } else {
+        void* w = nullptr;
+        cudaError_t e = cudaMalloc(&w, p->bytes_total);
+        if (e != cudaSuccess) return fail(XEB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        p->ws = static_cast<char*>(w);
+        p->owns = true;
+    }
+    p->ws_bytes = p->bytes_total;
+    build_launches(p);
+    {
+        std::string why;
+        if (!validate_launches(p, why)) {
+            if (p->owns) cudaFree(p->ws);
+            p->ws = nullptr;
+            return fail(XEB_EINVAL, "internal layout check failed: " + why);
+        }
+    }
+    char* tables = p->ws + p->off_tables;
+    // constant tables (host copies kept alive in the plan until the copies finish)
+    const std::vector<char> leafdata = leaf_host_data(p);
+    std::vector<int32_t> pi(p->an.pi.begin(), p->an.pi.end());
+    XEB_CUDA(cudaMemcpyAsync(p->ws + p->off_leafdata, leafdata.data(), leafdata.size(), cudaMemcpyHostToDevice, st));
+    XEB_CUDA(cudaMemcpyAsync(tables + p->t_trie_desc, p->trie.data(), p->trie.size() * sizeof(xebk::TrieDesc),
+                             cudaMemcpyHostToDevice, st));
+    XEB_CUDA(cudaMemcpyAsync(tables + p->t_internal, p->trie_internal.data(), p->trie_internal.size() * 4,
+                             cudaMemcpyHostToDevice, st));
+    XEB_CUDA(cudaMemcpyAsync(tables + p->t_leaf_desc, p->leafdesc.data(), p->leafdesc.size() * sizeof(xebk::LeafDesc),
+                             cudaMemcpyHostToDevice, st));
+    XEB_CUDA(cudaMemcpyAsync(tables + p->t_pi, pi.data(), pi.size() * 4, cudaMemcpyHostToDevice, st));
+    XEB_CUDA(cudaMemcpyAsync(tables + p->t_bits, p->bits.data(), p->k * 8, cudaMemcpyHostToDevice, st));
+    XEB_CUDA(cudaMemsetAsync(tables + p->t_err, 0, 4, st));
+    XEB_CUDA(cudaStreamSynchronize(st));
+    p->bound = true;
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_set_bitstrings(xeb_plan_s* p, const uint64_t* bits_dev, size_t k, uintptr_t stream) {
+    xeb_status s = check_bound(p);
+    if (s != XEB_OK) return s;
+    if (k != p->k) return fail(XEB_EINVAL, "k differs from the plan's k");
+    if (!bits_dev) return fail(XEB_EINVAL, "bitstrings pointer is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* tables = p->ws + p->off_tables;
+    XEB_CUDA(cudaMemcpyAsync(tables + p->t_bits, bits_dev, k * 8, cudaMemcpyDeviceToDevice, st));
+    return build_tables(p, st);
+}
+
+extern "C" xeb_status xeb_amplitudes(xeb_plan_s* p, double* out_dev, uintptr_t stream) {
+    xeb_status s = check_bound(p);
+    if (s != XEB_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!p->tables_ready) {
+        s = build_tables(p, st);
+        if (s != XEB_OK) return s;
+    }
+    double2* out = out_dev ? reinterpret_cast<double2*>(out_dev)
+                           : reinterpret_cast<double2*>(p->ws + p->off_tables + p->t_amps);
+    s = p->elem == 8 ? run_slices<float2>(p, out, st) : run_slices<double2>(p, out, st);
+    if (s == XEB_OK) p->amps_ready = true;
+    return s;
+}
+
+extern "C" xeb_status xeb_fidelity(xeb_plan_s* p, double* F, double* m1, double* m2, uintptr_t stream) {
+    xeb_status s = check_bound(p);
+    if (s != XEB_OK) return s;
+    if (!p->amps_ready) return fail(XEB_EINVAL, "no amplitudes computed yet");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* tables = p->ws + p->off_tables;
+    double res[4];
+    int32_t err = 0;
+    XEB_CUDA(cudaMemcpyAsync(res, tables + p->t_result, 32, cudaMemcpyDeviceToHost, st));
+    XEB_CUDA(cudaMemcpyAsync(&err, tables + p->t_err, 4, cudaMemcpyDeviceToHost, st));
+    XEB_CUDA(cudaStreamSynchronize(st));
+    if (err) return fail(XEB_EDEVICE, "device key tables disagree with the plan's counts (node " +
+                                           std::to_string(err - 1) + ")");
+    if (F) *F = res[0];
+    if (m1) *m1 = res[1];
+    if (m2) *m2 = res[2];
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_run(xeb_plan_s* p, const uint64_t* bits_host, size_t k, double* amps_host, double* F,
+                              uintptr_t stream) {
+    xeb_status s = check_bound(p);
+    if (s != XEB_OK) return s;
+    if (k != p->k) return fail(XEB_EINVAL, "k differs from the plan's k");
+    if (!bits_host) return fail(XEB_EINVAL, "bitstrings pointer is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* tables = p->ws + p->off_tables;
+    XEB_CUDA(cudaMemcpyAsync(tables + p->t_bits, bits_host, k * 8, cudaMemcpyHostToDevice, st));
+    s = build_tables(p, st);
+    if (s != XEB_OK) return s;
+    double* amps_dev = reinterpret_cast<double*>(tables + p->t_amps);
+    s = xeb_amplitudes(p, amps_dev, stream);
+    if (s != XEB_OK) return s;
+    if (amps_host) XEB_CUDA(cudaMemcpyAsync(amps_host, amps_dev, k * 16, cudaMemcpyDeviceToHost, st));
+    return xeb_fidelity(p, F, nullptr, nullptr, stream);
+}
+
+extern "C" xeb_status xeb_plan_keys(xeb_plan_s* p, int node, int32_t* key, int32_t* uL, int32_t* uR, uintptr_t stream) {
+    xeb_status s = check_bound(p);
+    if (s != XEB_OK) return s;
+    if (node < 0 || node >= int(p->tree.size())) return fail(XEB_EINVAL, "node out of range");
+    const int v = p->an.L + node;
+    const int ti = p->trie_of_node[v];
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* tables = p->ws + p->off_tables;
+    if (ti < 0) {  // no output bits: a single key
+        if (key) std::fill(key, key + p->k, 0);
+        if (uL) uL[0] = 0;
+        if (uR) uR[0] = 0;
+        return XEB_OK;
+    }
+    const xebk::TrieDesc& d = p->trie[ti];
+    if (key) XEB_CUDA(cudaMemcpyAsync(key, tables + d.key_off, p->k * 4, cudaMemcpyDeviceToHost, st));
+    if (uL) XEB_CUDA(cudaMemcpyAsync(uL, tables + d.uL_off, size_t(d.kv) * 4, cudaMemcpyDeviceToHost, st));
+    if (uR) XEB_CUDA(cudaMemcpyAsync(uR, tables + d.uR_off, size_t(d.kv) * 4, cudaMemcpyDeviceToHost, st));
+    XEB_CUDA(cudaStreamSynchronize(st));
+    return XEB_OK;
+}

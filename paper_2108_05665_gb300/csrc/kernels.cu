@@ -1,0 +1,517 @@
+// CUDA kernels of the memoized multi-amplitude contraction (sm_103a).
+//
+//  a1  k_trie_keys / k_trie_links : memo key tables.  A subexpression is
+//      evaluated once per distinct value of its variables (Sec. "Multi-tensor
+//      contraction algorithm"); keys are ranks of the node's output-bit range
+//      read as a number, i.e. the lexicographic order of App. C (Alg. 3).
+//  a2  k_leaves      : leaf tensors projected on output bits and sliced legs.
+//  a3  k_permute     : leg permutation of complex tensors (legs have dim 2, so
+//      a permutation of the index bits), tiled through shared memory so both
+//      the reads and the writes are contiguous runs.
+//  a4  k_gemm_*      : the pairwise contraction T*S of Eq. (elem-cont) as one
+//      complex GEMM per key, C_u = A_{uL(u)} B_{uR(u)}, FP32 (or FP64) FMA.
+//  a5  k_gemm_tail   : tiny near-root contractions, a warp per key with a
+//      shuffle reduction.
+//  a6  k_root_accum  : FP64 accumulation of the root over slices (Sec.
+//      "Slicing": contract per value of the fixed legs, then sum).
+//  a7  k_gather_xeb / k_xeb_final : amplitudes in input order and the linear
+//      XEB F = 2^n/k sum_i p(s_i) - 1 of Eq. (1), FP64, fixed reduction order.
+#include "kernels.cuh"
+
+namespace xebk {
+
+// ---- complex helpers -----------------------------------------------------------
+__device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ double2 cfma(double2 acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+    return acc;
+}
+template <typename T> __device__ __forceinline__ T czero();
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float2 shfl_down(float2 v, int d) {
+    v.x = __shfl_down_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+    return v;
+}
+__device__ __forceinline__ double2 shfl_down(double2 v, int d) {
+    v.x = __shfl_down_sync(0xffffffffu, v.x, d);
+    v.y = __shfl_down_sync(0xffffffffu, v.y, d);
+    return v;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+static inline int grid_for(int64_t work, int per_block, int cap) {
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return int(b);
+}
+
+// ---- a1: memo key tables ---------------------------------------------------------
+
+// Block-wide exclusive scan of one int per thread (blockDim.x <= 1024).
+__device__ int block_exclusive_scan(int v, int* total) {
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        int t = lane < nw ? warp_tot[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t += y;
+        }
+        warp_tot[lane] = t;  // inclusive
+    }
+    __syncthreads();
+    const int before = wid > 0 ? warp_tot[wid - 1] : 0;
+    *total = warp_tot[((blockDim.x + 31) >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_trie_keys(const TrieDesc* desc, const uint64_t* bits, int k,
+                                                     int kpad, const int32_t* pi, char* tables,
+                                                     int32_t* err) {
+    extern __shared__ uint64_t sm_trie[];
+    uint64_t* val = sm_trie;
+    int32_t* idx = reinterpret_cast<int32_t*>(sm_trie + kpad);
+    const TrieDesc d = desc[blockIdx.x];
+    for (int i = threadIdx.x; i < kpad; i += blockDim.x) {
+        if (i < k) {
+            const uint64_t s = bits[i];
+            uint64_t v = 0;
+            for (int t = d.a; t < d.b; ++t) v = (v << 1) | ((s >> pi[t]) & 1ull);
+            val[i] = v;
+            idx[i] = i;
+        } else {
+            val[i] = ~0ull;
+            idx[i] = 0x7fffffff;
+        }
+    }
+    __syncthreads();
+    // bitonic sort of (val, idx) ascending
+    for (int size = 2; size <= kpad; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (kpad >> 1); t += blockDim.x) {
+                const int i = 2 * t - (t & (stride - 1));
+                const int j = i + stride;
+                const bool up = (i & size) == 0;
+                const uint64_t vi = val[i], vj = val[j];
+                const int32_t ii = idx[i], ij = idx[j];
+                const bool gt = vi > vj || (vi == vj && ii > ij);
+                if (gt == up) {
+                    val[i] = vj; val[j] = vi;
+                    idx[i] = ij; idx[j] = ii;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ranks of distinct values
+    const int chunk = (k + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * chunk;
+    const int hi = min(k, lo + chunk);
+    int cnt = 0;
+    for (int i = lo; i < hi; ++i) cnt += (i == 0 || val[i] != val[i - 1]);
+    int total = 0;
+    int rank = block_exclusive_scan(cnt, &total) - 1;
+    int32_t* key = reinterpret_cast<int32_t*>(tables + d.key_off);
+    uint64_t* uniq = reinterpret_cast<uint64_t*>(tables + d.uniq_off);
+    int32_t* rep = reinterpret_cast<int32_t*>(tables + d.rep_off);
+    for (int i = lo; i < hi; ++i) {
+        if (i == 0 || val[i] != val[i - 1]) {
+            ++rank;
+            if (rank < d.kv) {
+                uniq[rank] = val[i];
+                rep[rank] = idx[i];
+            }
+        }
+        key[idx[i]] = min(rank, d.kv - 1);  // ids stay inside planned tables
+    }
+    for (int r = total + threadIdx.x; r < d.kv; r += blockDim.x) {  // count mismatch: keep tables valid
+        uniq[r] = 0;
+        rep[r] = 0;
+    }
+    if (threadIdx.x == 0 && total != d.kv) atomicExch(err, 1 + int(blockIdx.x));
+}
+
+__global__ void k_trie_links(const TrieDesc* desc, const int* internal, char* tables) {
+    const TrieDesc d = desc[internal[blockIdx.y]];
+    const int32_t* rep = reinterpret_cast<const int32_t*>(tables + d.rep_off);
+    const int32_t* lk = d.l_key_off >= 0 ? reinterpret_cast<const int32_t*>(tables + d.l_key_off) : nullptr;
+    const int32_t* rk = d.r_key_off >= 0 ? reinterpret_cast<const int32_t*>(tables + d.r_key_off) : nullptr;
+    int32_t* uL = reinterpret_cast<int32_t*>(tables + d.uL_off);
+    int32_t* uR = reinterpret_cast<int32_t*>(tables + d.uR_off);
+    int32_t* gs = reinterpret_cast<int32_t*>(tables + d.gstart_off);
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < d.kv; u += gridDim.x * blockDim.x) {
+        const int rp = rep[u];
+        const int l = lk ? lk[rp] : 0;
+        const int r = rk ? rk[rp] : 0;
+        uL[u] = l;
+        uR[u] = r;
+        const int lprev = u > 0 ? (lk ? lk[rep[u - 1]] : 0) : -1;
+        if (u == 0 || l != lprev) gs[l] = u;
+        if (u == d.kv - 1) gs[d.kL] = d.kv;
+    }
+}
+
+cudaError_t launch_trie_keys(const TrieDesc* d_desc, int n_nodes, const uint64_t* bits, int k,
+                             const int32_t* pi, char* tables, int32_t* err, cudaStream_t st) {
+    if (n_nodes == 0) return cudaSuccess;
+    int kpad = 2;
+    while (kpad < k) kpad <<= 1;
+    const size_t smem = size_t(kpad) * (sizeof(uint64_t) + sizeof(int32_t));
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_trie_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(size_t(kMaxTrieK) * 12));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_trie_keys<<<n_nodes, 1024, smem, st>>>(d_desc, bits, k, kpad, pi, tables, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trie_links(const TrieDesc* d_desc, const int* d_internal, int n_internal, int max_kv,
+                              char* tables, cudaStream_t st) {
+    if (n_internal == 0) return cudaSuccess;
+    dim3 grid(grid_for(max_kv, 256, 64), n_internal);
+    k_trie_links<<<grid, 256, 0, st>>>(d_desc, d_internal, tables);
+    return cudaGetLastError();
+}
+
+// ---- a2: leaves ------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_leaves(const LeafDesc* desc, const T* leafdata, T* arena, const char* tables,
+                         int64_t slice) {
+    const LeafDesc d = desc[blockIdx.x];
+    const uint64_t* uniq = d.uniq_off >= 0 ? reinterpret_cast<const uint64_t*>(tables + d.uniq_off) : nullptr;
+    int64_t sl_base = 0;
+    for (int t = 0; t < d.n_sl; ++t)
+        if ((slice >> d.sl_bit[t]) & 1) sl_base |= int64_t(1) << d.sl_pos[t];
+    const int64_t per = int64_t(1) << d.r;
+    for (int64_t e = threadIdx.x; e < int64_t(d.kv) * per; e += blockDim.x) {
+        const int64_t u = e >> d.r, x = e & (per - 1);
+        const uint64_t v = uniq ? uniq[u] : 0;
+        int64_t src = (int64_t(v) << (d.n_canon - d.n_out)) | sl_base;
+        for (int j = 0; j < d.r; ++j)
+            if ((x >> j) & 1) src |= int64_t(1) << d.src_pos[j];
+        arena[d.dst_off + e] = leafdata[d.src_off + src];
+    }
+}
+
+template <typename T>
+cudaError_t launch_leaves(const LeafDesc* d_desc, int n_leaves, const T* leafdata, T* arena,
+                          const char* tables, int64_t slice, cudaStream_t st) {
+    k_leaves<T><<<n_leaves, 128, 0, st>>>(d_desc, leafdata, arena, tables, slice);
+    return cudaGetLastError();
+}
+
+// ---- a3: permutation ----------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute(const PermDesc p, const T* __restrict__ src,
+                                                 T* __restrict__ dst, int64_t n_tiles) {
+    extern __shared__ __align__(16) unsigned char sm_perm[];
+    T* tile = reinterpret_cast<T*>(sm_perm);
+    const int tsz = 1 << p.u;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t key = t >> p.n_outer;
+        const int64_t o = t & ((int64_t(1) << p.n_outer) - 1);
+        int64_t so = key << p.r, dso = key << p.r;
+        for (int i = 0; i < p.n_outer; ++i)
+            if ((o >> i) & 1) {
+                so |= int64_t(1) << p.outer_src[i];
+                dso |= int64_t(1) << p.outer_dst[i];
+            }
+        for (int e = threadIdx.x; e < tsz; e += blockDim.x) {
+            int64_t off = so;
+            for (int i = 0; i < p.u; ++i)
+                if ((e >> i) & 1) off |= int64_t(1) << p.usrc[i];
+            tile[e] = src[off];
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < tsz; f += blockDim.x) {
+            int e = 0;
+            int64_t off = dso;
+            for (int i = 0; i < p.u; ++i)
+                if ((f >> i) & 1) {
+                    e |= 1 << p.udst_e[i];
+                    off |= int64_t(1) << p.udst[i];
+                }
+            dst[off] = tile[e];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_permute(const PermDesc& p, const T* src, T* dst, cudaStream_t st) {
+    const int64_t n_tiles = p.keys << p.n_outer;
+    const int grid = grid_for(n_tiles, 1, 152 * 16);
+    k_permute<T><<<grid, 256, sizeof(T) << p.u, st>>>(p, src, dst, n_tiles);
+    return cudaGetLastError();
+}
+
+// ---- a4/a5: contractions ----------------------------------------------------------
+
+template <typename T>
+__global__ void k_gemm_generic(const GemmDesc g, T* __restrict__ arena) {
+    const int64_t total = g.kv * g.M * g.N;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t n = e % g.N;
+        const int64_t rest = e / g.N;
+        const int64_t m = rest % g.M;
+        const int64_t u = rest / g.M;
+        const int64_t ua = g.uL ? g.uL[u] : 0;
+        const int64_t ub = g.uR ? g.uR[u] : 0;
+        const T* a = arena + g.a_off + ua * g.sa_key + m * g.sa_m;
+        const T* b = arena + g.b_off + ub * g.sb_key + n * g.sb_n;
+        T acc = czero<T>();
+        for (int64_t k = 0; k < g.K; ++k) acc = cfma(acc, a[k * g.sa_k], b[k * g.sb_k]);
+        arena[g.c_off + u * g.sc_key + m * g.sc_m + n * g.sc_n] = acc;
+    }
+}
+
+// 64 x 64 output tile per CTA, 8-deep K slices, 256 threads with 4 x 4 each.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_tiled(const GemmDesc g, T* __restrict__ arena,
+                                                    int64_t mt, int64_t nt) {
+    __shared__ T As[8][64];
+    __shared__ T Bs[8][64];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t n_tiles = g.kv * mt * nt;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t u = tile % g.kv;
+        const int64_t rest = tile / g.kv;
+        const int64_t m0 = (rest % mt) * 64;
+        const int64_t n0 = (rest / mt) * 64;
+        const int64_t ua = g.uL ? g.uL[u] : 0;
+        const int64_t ub = g.uR ? g.uR[u] : 0;
+        const T* A = arena + g.a_off + ua * g.sa_key;
+        const T* B = arena + g.b_off + ub * g.sb_key;
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = czero<T>();
+        for (int64_t k0 = 0; k0 < g.K; k0 += 8) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = tid + r * 256;
+                int mm, kk;
+                if (g.sa_k == 1) { kk = e & 7; mm = e >> 3; } else { mm = e & 63; kk = e >> 6; }
+                const int64_t m = m0 + mm, k = k0 + kk;
+                As[kk][mm] = (m < g.M && k < g.K) ? A[m * g.sa_m + k * g.sa_k] : czero<T>();
+                int nn, kb;
+                if (g.sb_n == 1) { nn = e & 63; kb = e >> 6; } else { kb = e & 7; nn = e >> 3; }
+                const int64_t n = n0 + nn, k2 = k0 + kb;
+                Bs[kb][nn] = (n < g.N && k2 < g.K) ? B[k2 * g.sb_k + n * g.sb_n] : czero<T>();
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                T af[4], bf[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) af[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bf[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = cfma(acc[i][j], af[i], bf[j]);
+            }
+            __syncthreads();
+        }
+        T* C = arena + g.c_off + u * g.sc_key;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t m = m0 + ty * 4 + i;
+            if (m >= g.M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t n = n0 + tx * 4 + j;
+                if (n < g.N) C[m * g.sc_m + n * g.sc_n] = acc[i][j];
+            }
+        }
+    }
+}
+
+// N == 1: one thread per (left-key group, row m); the A row is shared by all
+// keys of the group (keys are sorted by their left key, so groups are runs).
+template <typename T>
+__global__ void k_gemm_gemv(const GemmDesc g, T* __restrict__ arena) {
+    const int64_t total = g.n_groups * g.M;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t m = e % g.M;
+        const int64_t grp = e / g.M;
+        const int64_t u0 = g.gstart ? g.gstart[grp] : 0;
+        const int64_t u1 = g.gstart ? g.gstart[grp + 1] : g.kv;
+        const int64_t ua = g.uL ? g.uL[u0] : 0;
+        const T* a = arena + g.a_off + ua * g.sa_key + m * g.sa_m;
+        for (int64_t u = u0; u < u1; ++u) {
+            const int64_t ub = g.uR ? g.uR[u] : 0;
+            const T* b = arena + g.b_off + ub * g.sb_key;
+            T acc = czero<T>();
+            for (int64_t k = 0; k < g.K; ++k) acc = cfma(acc, a[k * g.sa_k], b[k * g.sb_k]);
+            arena[g.c_off + u * g.sc_key + m * g.sc_m] = acc;
+        }
+    }
+}
+
+// M == N == 1: a warp per key, lanes split K, shuffle reduction.
+template <typename T>
+__global__ void k_gemm_tail(const GemmDesc g, T* __restrict__ arena) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t u = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; u < g.kv; u += warps) {
+        const int64_t ua = g.uL ? g.uL[u] : 0;
+        const int64_t ub = g.uR ? g.uR[u] : 0;
+        const T* a = arena + g.a_off + ua * g.sa_key;
+        const T* b = arena + g.b_off + ub * g.sb_key;
+        T acc = czero<T>();
+        for (int64_t k = lane; k < g.K; k += 32) acc = cfma(acc, a[k * g.sa_k], b[k * g.sb_k]);
+        for (int d = 16; d > 0; d >>= 1) acc = cadd(acc, shfl_down(acc, d));
+        if (lane == 0) arena[g.c_off + u * g.sc_key] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t launch_gemm(int kernel, const GemmDesc& g, T* arena, cudaStream_t st) {
+    const int cap = 152 * 32;
+    switch (kernel) {
+        case GK_TILED: {
+            const int64_t mt = (g.M + 63) / 64, nt = (g.N + 63) / 64;
+            k_gemm_tiled<T><<<grid_for(g.kv * mt * nt, 1, cap), 256, 0, st>>>(g, arena, mt, nt);
+            break;
+        }
+        case GK_GEMV:
+            k_gemm_gemv<T><<<grid_for(g.n_groups * g.M, 256, cap), 256, 0, st>>>(g, arena);
+            break;
+        case GK_TAIL:
+            k_gemm_tail<T><<<grid_for(g.kv * 32, 256, cap), 256, 0, st>>>(g, arena);
+            break;
+        default:
+            k_gemm_generic<T><<<grid_for(g.kv * g.M * g.N, 256, cap), 256, 0, st>>>(g, arena);
+    }
+    return cudaGetLastError();
+}
+
+// ---- a6/a7 -------------------------------------------------------------------------
+
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+
+template <typename T>
+__global__ void k_root_accum(const T* root, double2* acc, int64_t kv) {
+    for (int64_t u = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; u < kv; u += int64_t(gridDim.x) * blockDim.x) {
+        const double2 r = to_d2(root[u]);
+        double2 a = acc[u];
+        a.x += r.x;
+        a.y += r.y;
+        acc[u] = a;
+    }
+}
+
+template <typename T>
+cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStream_t st) {
+    k_root_accum<T><<<grid_for(kv, 256, 1024), 256, 0, st>>>(root, acc, kv);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k,
+                                                    double2* amps, double* partials) {
+    __shared__ double s1[256], s2[256];
+    double a1 = 0.0, a2 = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < k; i += int64_t(gridDim.x) * blockDim.x) {
+        const double2 a = acc[key_root[i]];
+        amps[i] = a;
+        const double p = a.x * a.x + a.y * a.y;
+        a1 += p;
+        a2 += p * p;
+    }
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int d = 128; d > 0; d >>= 1) {
+        if (threadIdx.x < d) {
+            s1[threadIdx.x] += s1[threadIdx.x + d];
+            s2[threadIdx.x] += s2[threadIdx.x + d];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = s1[0];
+        partials[2 * blockIdx.x + 1] = s2[0];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_xeb_final(const double* partials, int nb, int64_t k, int n,
+                                                   double* result) {
+    __shared__ double s1[256], s2[256];
+    double a1 = 0.0, a2 = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        a1 += partials[2 * b];
+        a2 += partials[2 * b + 1];
+    }
+    s1[threadIdx.x] = a1;
+    s2[threadIdx.x] = a2;
+    __syncthreads();
+    for (int d = 128; d > 0; d >>= 1) {
+        if (threadIdx.x < d) {
+            s1[threadIdx.x] += s1[threadIdx.x + d];
+            s2[threadIdx.x] += s2[threadIdx.x + d];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double scale = ldexp(1.0, n);
+        const double mean = scale * s1[0] / double(k);
+        result[0] = mean - 1.0;
+        result[1] = mean;
+        result[2] = scale * scale * s2[0] / double(k);
+    }
+}
+
+cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k, double2* amps,
+                              double* partials, int n_blocks, double* result, int n_qubits, cudaStream_t st) {
+    k_gather_xeb<<<n_blocks, 256, 0, st>>>(acc, key_root, k, amps, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_xeb_final<<<1, 256, 0, st>>>(partials, n_blocks, k, n_qubits, result);
+    return cudaGetLastError();
+}
+
+// ---- instantiations ------------------------------------------------------------------
+template cudaError_t launch_leaves<float2>(const LeafDesc*, int, const float2*, float2*, const char*, int64_t, cudaStream_t);
+template cudaError_t launch_leaves<double2>(const LeafDesc*, int, const double2*, double2*, const char*, int64_t, cudaStream_t);
+template cudaError_t launch_permute<float2>(const PermDesc&, const float2*, float2*, cudaStream_t);
+template cudaError_t launch_permute<double2>(const PermDesc&, const double2*, double2*, cudaStream_t);
+template cudaError_t launch_gemm<float2>(int, const GemmDesc&, float2*, cudaStream_t);
+template cudaError_t launch_gemm<double2>(int, const GemmDesc&, double2*, cudaStream_t);
+template cudaError_t launch_root_accum<float2>(const float2*, double2*, int64_t, cudaStream_t);
+template cudaError_t launch_root_accum<double2>(const double2*, double2*, int64_t, cudaStream_t);
+
+}  // namespace xebk

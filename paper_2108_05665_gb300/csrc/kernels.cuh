@@ -1,0 +1,86 @@
+// Device-side descriptors and launch wrappers of the contraction kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xebk {
+
+constexpr int kMaxTrieK = 16384;  // bitstrings per single-CTA key-table sort
+
+// Memo key table of one tree node that depends on output bits (a1).
+struct TrieDesc {
+    int a, b;            // range of the node's bits in pi
+    int kv;              // planned number of distinct values
+    int is_internal;
+    int64_t key_off;     // int32 [k]   key id of every bitstring
+    int64_t uniq_off;    // uint64 [kv] value of every key (ascending)
+    int64_t rep_off;     // int32 [kv]  one bitstring having that key
+    int64_t uL_off;      // int32 [kv]  left child's key id (internal)
+    int64_t uR_off;      // int32 [kv]  right child's key id (internal)
+    int64_t gstart_off;  // int32 [kL+1] first key of every left-key group (internal)
+    int64_t l_key_off;   // left child's key array, -1 if the child has no bits
+    int64_t r_key_off;   // right child's key array, -1 if the child has no bits
+    int kL;              // left child's key count
+    int pad;
+};
+
+// Leaf materialisation (a2): projected leaf tensor per key and slice.
+struct LeafDesc {
+    int64_t dst_off;     // element offset in the arena
+    int64_t src_off;     // element offset in the leaf data
+    int r;               // stored rank (bond legs not sliced)
+    int n_out;           // output bits of the leaf
+    int n_canon;         // canonical rank = n_out + all bond legs (sliced too)
+    int kv;
+    int src_pos[8];      // stored bit j (0 = fastest) -> canonical bit position
+    int n_sl;
+    int sl_pos[4];       // canonical bit position of the leaf's sliced legs
+    int sl_bit[4];       // their bit in the slice index
+    int64_t uniq_off;    // trie uniq table of the leaf (-1 if no output bits)
+};
+
+// Tiled bit permutation (a3): dst bit j <- src bit perm[j].
+struct PermDesc {
+    int r, u, n_outer;
+    int usrc[12];        // tile bit i (src order) -> src bit position
+    int udst_e[12];      // dst-order tile bit i -> src-order tile bit
+    int udst[12];        // dst-order tile bit i -> dst bit position
+    int outer_src[48];   // outer bit i -> src bit position
+    int outer_dst[48];   // outer bit i -> dst bit position
+    int64_t keys;
+};
+
+// One pairwise contraction, for u < kv: C_u = A_{uL(u)} (M x K) * B_{uR(u)} (K x N).
+struct GemmDesc {
+    int64_t M, N, K, kv;
+    int64_t a_off, sa_key, sa_m, sa_k;
+    int64_t b_off, sb_key, sb_k, sb_n;
+    int64_t c_off, sc_key, sc_m, sc_n;
+    const int32_t* uL;   // nullptr -> 0
+    const int32_t* uR;   // nullptr -> 0
+    const int32_t* gstart;  // groups of keys by uL (nullptr -> one group)
+    int64_t n_groups;
+};
+
+enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3 };
+
+// ---- launch wrappers (all asynchronous on `st`) --------------------------------
+cudaError_t launch_trie_keys(const TrieDesc* d_desc, int n_nodes, const uint64_t* bits, int k,
+                             const int32_t* pi, char* tables, int32_t* err, cudaStream_t st);
+cudaError_t launch_trie_links(const TrieDesc* d_desc, const int* d_internal, int n_internal,
+                              int max_kv, char* tables, cudaStream_t st);
+template <typename T>
+cudaError_t launch_leaves(const LeafDesc* d_desc, int n_leaves, const T* leafdata, T* arena,
+                          const char* tables, int64_t slice, cudaStream_t st);
+template <typename T>
+cudaError_t launch_permute(const PermDesc& p, const T* src, T* dst, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gemm(int kernel, const GemmDesc& g, T* arena, cudaStream_t st);
+template <typename T>
+cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStream_t st);
+cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k,
+                              double2* amps, double* partials, int n_blocks, double* result,
+                              int n_qubits, cudaStream_t st);
+
+}  // namespace xebk

@@ -1,0 +1,115 @@
+// Host-side planning: circuit -> tensor network, contraction trees, exact
+// memoized evaluation counts, slicing, operand layouts and the device program.
+#pragma once
+
+#include <array>
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "xeb.h"
+
+namespace xebp {
+
+using cd = std::complex<double>;
+
+// One leaf of the fused circuit network (convention of include/xeb.h).
+// Tensor axes: out_q (listed order) then legs; row-major, first axis slowest.
+struct Leaf {
+    std::vector<int> out_q;
+    std::vector<int> legs;
+    std::vector<int> qubits;  // qubits of the gate the leaf came from
+    std::vector<cd> t;
+};
+
+struct Network {
+    int n = 0;
+    int n_legs = 0;
+    std::vector<Leaf> leaves;
+};
+
+bool build_network(const xeb_circuit* c, Network& net, std::string& err);
+
+using Tree = std::vector<std::array<int, 2>>;  // post-order (left, right) pairs
+
+// Per tree node (uniform ids: leaf j -> j, internal i -> L + i).
+struct Node {
+    int l = -1, r = -1, parent = -1;
+    std::vector<int> legs;  // legs of the node tensor (sliced legs removed)
+    int q = 0;              // legs summed at this node (internal)
+    uint64_t qmask = 0;     // output qubits the subtree depends on
+    int a = 0, b = 0;       // range in pi
+    int64_t kv = 1;         // exact number of distinct values of its bits
+};
+
+struct Analysis {
+    int L = 0;
+    std::vector<Node> nodes;
+    std::vector<int> pi;
+};
+
+// Distinct-count oracle over the plan's bitstrings, cached by qubit mask.
+struct DistinctCounter {
+    const uint64_t* bs = nullptr;
+    size_t k = 0;
+    std::unordered_map<uint64_t, int64_t> cache;
+    std::vector<uint64_t> scratch;
+    int64_t count(uint64_t mask);
+};
+
+bool check_tree(const Tree& t, int n_leaves, std::string& err);
+bool analyze(const Network& net, const Tree& tree, const std::vector<int>& sliced,
+             Analysis& an, std::string& err);
+void fill_counts(Analysis& an, DistinctCounter& dc);
+
+// ---- device program ----------------------------------------------------------
+enum OpKind { OP_PERM = 1, OP_GEMM = 2 };
+
+struct Op {
+    int kind = 0;
+    int node = -1;          // uniform id of the node produced (GEMM) / permuted (PERM)
+    // PERM: dst[key][x'] = src[key][x] where dst bit j comes from src bit perm[j]
+    int src_buf = -1, dst_buf = -1;
+    int r = 0;
+    int64_t keys = 0;
+    std::vector<int> perm;
+    // GEMM: for u < kv: C_u = A_{uL(u)} (M x K) * B_{uR(u)} (K x N)
+    int a_buf = -1, b_buf = -1, c_buf = -1;
+    int a_node = -1, b_node = -1;
+    int64_t M = 1, N = 1, K = 1, kv = 1;
+    int64_t sa_key = 0, sa_m = 0, sa_k = 0;
+    int64_t sb_key = 0, sb_k = 0, sb_n = 0;
+    int64_t sc_key = 0, sc_m = 0, sc_n = 0;
+};
+
+struct Buffer {
+    int64_t elems = 0;   // complex elements
+    int64_t off = -1;    // element offset in the arena
+    int first = -1, last = -1;
+};
+
+struct Program {
+    std::vector<Op> ops;
+    std::vector<Buffer> bufs;
+    std::vector<int> node_buf;                 // final buffer of each node's tensor
+    std::vector<std::vector<int>> layout;      // stored leg order per node (slowest first)
+    int64_t arena_elems = 0;
+    double permute_elems = 0;
+};
+
+void build_program(const Analysis& an, Program& prog);
+void plan_memory(Program& prog);  // emulation-mode allocator: exact arena peak
+
+struct Costs {
+    double C = 0, RW = 0, single = 0, perm = 0;
+};
+Costs tree_costs(const Analysis& an, const Program& prog, uint64_t k);
+
+// ---- planners ----------------------------------------------------------------
+Tree greedy_tree(const Network& net, DistinctCounter& dc, const std::vector<int>& sliced,
+                 uint64_t seed, double noise);
+bool sweep_tree(const Network& net, int block_qubits, int group_leaves, Tree& out);
+
+}  // namespace xebp
