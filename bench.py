@@ -1,0 +1,338 @@
+"""Benchmark of the memoized multi-amplitude contraction + linear XEB.
+
+One step = one pass of the whole hot path over one batch of bitstrings:
+memo key tables (a1), leaf projection (a2), every pairwise contraction of the
+tree with its permutations (a3-a5), FP64 root accumulation (a6) and the
+gathered amplitudes + linear XEB (a7).
+
+Workload (N=1): 5x6-grid random circuit, 14 cycles, 10,000 bitstrings
+(5,000 sampled from the ideal output distribution + 5,000 uniform), complex64
+tensors.  The bitstrings come from tests/golden/grid5x6_m14_k10000.npz
+(written by the oracle); the circuit is generated from its seed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32x3]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2108_05665_gb300 import inputs  # noqa: E402
+
+METRIC = "amplitudes/s & complex TFLOP/s, tensor-core split-prec vs plain FP32, 1 GB300"
+WORKLOAD = "grid5x6_m14_k10000"
+FIXTURE = os.path.join(ROOT, "tests", "golden", "grid5x6_m14_k10000.npz")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def workload_desc(w):
+    return ("%dx%d grid random circuit, %d cycles, fSim(pi/2,pi/6) + sqrt(X/Y/W); %d bitstrings "
+            "(%d ideal samples + %d uniform); memoized tree over all output bits"
+            % (w.rows, w.cols, w.cycles, w.k, int(w.k * w.ideal_fraction), w.k - int(w.k * w.ideal_fraction)))
+
+
+def load_bitstrings(w):
+    z = np.load(FIXTURE)
+    bits = np.asarray(z["bitstrings"], dtype=np.uint64)
+    assert len(bits) == w.k
+    return bits
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = max(mx, float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(circ, target_s=15.0):
+    """Time the FP64 state-vector oracle on the first gates of the circuit
+    (full 2^n state) and extrapolate to the whole circuit."""
+    from oracle import statevec
+    gates = circ.gates
+    g = 8
+    while True:
+        part = inputs.Circuit(circ.n_qubits, gates[:g])
+        t0 = time.perf_counter()
+        psi = statevec.state(part)
+        dt = time.perf_counter() - t0
+        del psi
+        if dt > target_s / 3 or g >= len(gates):
+            break
+        g = min(len(gates), int(g * max(2.0, target_s / max(dt, 1e-3) * 0.5)))
+    # per-gate cost: the 1q / 2q passes are both one sweep over the state
+    t_full = dt * len(gates) / g
+    return t_full, g, len(gates)
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = inputs.WORKLOADS[WORKLOAD]
+    circ = w.circuit()
+    from oracle import statevec
+    statevec.build()
+    times = []
+    for _ in range(args.warmup + args.steps):
+        t_full, g, G = cpu_oracle_sample(circ, target_s=args.ref_seconds)
+        times.append(t_full)
+    times = times[args.warmup:]
+    t = statistics.median(times)
+    value = w.k / t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": workload_desc(w)},
+            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
+                             "sample": "FP64 state-vector oracle on the first %d of %d gates of the circuit "
+                                       "(full 2^%d state), extrapolated linearly to all gates" % (g, G, w.n_qubits)},
+            "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_2108_05665_gb300 import binding as B, build
+    rank, world = dist_setup(args.gpus)
+    build.build()
+    B.load()
+    w = inputs.WORKLOADS[WORKLOAD]
+    circ = w.circuit()
+    bits = load_bitstrings(w)
+    prec = {"fp32": B.XEB_PREC_FP32, "tf32x3": B.XEB_PREC_TF32X3}[args.precision]
+    o = B.xeb_default_opts()
+    o.precision = prec
+    try:
+        plan = B.Plan(circ, bits, opts=o)
+        plan.bind()
+    except B.XebError as e:
+        if prec == B.XEB_PREC_TF32X3 and e.status == 5:
+            args.precision = "fp32"
+            o.precision = B.XEB_PREC_FP32
+            plan = B.Plan(circ, bits, opts=o)
+            plan.bind()
+        else:
+            raise
+    st = plan.stats()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    k = len(bits)
+    dev_bits = torch.from_numpy(bits.view(np.int64).copy()).cuda()
+    out = torch.empty(2 * k, dtype=torch.float64, device="cuda")
+
+    def step():
+        B.xeb_set_bitstrings(plan.handle, dev_bits.data_ptr(), k, sp)
+        B.xeb_amplitudes(plan.handle, out.data_ptr(), sp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    F, m1, m2 = B.xeb_fidelity(plan.handle, sp)
+    # ---- timed region (device-resident inputs) ----
+    B.xeb_plan_profile(plan.handle, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    prof = B.xeb_plan_profile_read(plan.handle)
+    B.xeb_plan_profile(plan.handle, False)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    value = world * k * args.steps / (ms_total / 1e3)
+    clocks = clk.summary()
+    # ---- end-to-end through the host entry point (pinned host buffers) ----
+    hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
+    ha = torch.empty(2 * k, dtype=torch.float64).pin_memory()
+    B.xeb_run(plan.handle, hb.data_ptr(), k, ha.data_ptr(), sp)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    e_steps = max(1, args.steps // 2)
+    for _ in range(e_steps):
+        Fe = B.xeb_run(plan.handle, hb.data_ptr(), k, ha.data_ptr(), sp)
+    torch.cuda.synchronize()
+    e_s = max_over_ranks(time.perf_counter() - e0, world)
+    e2e_value = world * k * e_steps / e_s
+    # ---- roofline of the dominant kernel class ----
+    pk, pk_kind = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, d = dom
+    per_launch_ms = d["ms"] / d["launches"]
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    if name in ("gemm_tc",):
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        peak = pk["bf16_tflops"] / 2.0  # tf32 = half of the bf16 dense rate
+        peak_note = "measured bf16 x nominal tf32/bf16 ratio 1/2 (" + pk_kind + ")"
+    elif name in ("gemm_tiled", "gemm_generic") and d["flops"] / max(d["bytes"], 1) > 12:
+        bound, unit = "alu", "TFLOP/s"
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
+        peak_note = "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_max
+    else:
+        bound, unit = "hbm", "GB/s"
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        peak = pk["hbm_gbs"]
+        peak_note = "measured copy bandwidth (" + pk_kind + ")"
+    eff_tflops = st["flops_per_slice"] * st["n_slices"] * args.steps * world / (ms_total / 1e3) / 1e12
+    launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32x3": "tf32x3"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "desc": workload_desc(w), "precision": args.precision,
+                   "planner": ["given", "greedy", "sweep"][st["planner_used"]], "n_slices": st["n_slices"],
+                   "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
+                   "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},
+        "complex_tflops": eff_tflops,
+        "flops_per_step": st["flops_per_slice"] * st["n_slices"],
+        "memo_gain": st["single_amp_flops"] / max(st["flops_per_slice"], 1.0),
+        "F": F, "F_e2e": Fe,
+        "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * k,
+                "d2h_bytes_per_step": 16 * k + 32},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+                     "per_launch_ms": per_launch_ms,
+                     "share_of_step": d["ms"] / ms_total},
+        "kernels": {kname: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                    for kname, v in prof.items()},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_full, g, G = cpu_oracle_sample(circ)
+        line["cpu_baseline"] = {"value": k / t_full, "unit": "amplitudes/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": "FP64 state-vector oracle on the first %d of %d gates (full 2^%d state), "
+                                          "extrapolated linearly to the whole circuit" % (g, G, w.n_qubits)}
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

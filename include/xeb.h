@@ -197,6 +197,34 @@ xeb_status xeb_run(struct xeb_plan_s* plan, const uint64_t* bitstrings_host, siz
 xeb_status xeb_plan_keys(struct xeb_plan_s* plan, int node, int32_t* key_of_bitstring,
                          int32_t* uL, int32_t* uR, uintptr_t stream);
 
+/* Kernel classes reported by xeb_plan_profile_read. */
+enum {
+    XEB_KC_TRIE = 0,          /* a1 key tables                                   */
+    XEB_KC_LEAVES = 1,        /* a2 leaf projection                              */
+    XEB_KC_PERMUTE = 2,       /* a3 leg permutation                              */
+    XEB_KC_GEMM_TILED = 3,    /* a4 FP32/FP64 SIMT tiled complex GEMM            */
+    XEB_KC_GEMM_GEMV = 4,     /* a4 grouped matrix-vector (memo trie levels)     */
+    XEB_KC_GEMM_TAIL = 5,     /* a5 warp-per-key dot products                    */
+    XEB_KC_GEMM_GENERIC = 6,  /* a4 small contractions                           */
+    XEB_KC_ACCUM = 7,         /* a6 FP64 accumulation over slices                */
+    XEB_KC_XEB = 8,           /* a7 gather + linear XEB                          */
+    XEB_KC_GEMM_TC = 9,       /* a4 tcgen05 split-precision complex GEMM         */
+    XEB_N_KC = 16
+};
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing of the plan's
+ * kernels on the stream they are launched on (adds two event records per
+ * launch; host only otherwise).  Enabling resets the accumulated totals. */
+xeb_status xeb_plan_profile(struct xeb_plan_s* plan, int enable);
+
+/* Accumulated totals per kernel class since profiling was enabled: device
+ * milliseconds, launches, algorithmic flops (8 per complex multiply-add) and
+ * algorithmic bytes (each operand tensor read once, each result written
+ * once).  Each output is a host array of XEB_N_KC doubles (may be NULL).
+ * Synchronises on the recorded events. */
+xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* launches, double* flops,
+                                 double* bytes);
+
 /* Thread-local message of the last failure in this thread. */
 const char* xeb_last_error(void);
 

@@ -92,6 +92,8 @@ _PROTOS = {
     "xeb_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, _dblp,
                                ctypes.c_void_p]),
     "xeb_plan_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_void_p]),
+    "xeb_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "xeb_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp, _dblp, _dblp]),
     "xeb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -246,6 +248,25 @@ def xeb_plan_keys(plan, node: int, k: int, kv: int, stream: int):
     _check(load().xeb_plan_keys(plan, node, _ptr(key, ctypes.c_int32), _ptr(uL, ctypes.c_int32),
                                 _ptr(uR, ctypes.c_int32), ctypes.c_void_p(stream or None)))
     return key, uL[:kv], uR[:kv]
+
+
+KERNEL_CLASSES = ["trie", "leaves", "permute", "gemm_tiled", "gemm_gemv", "gemm_tail", "gemm_generic",
+                  "accum", "xeb", "gemm_tc"]
+XEB_N_KC = 16
+
+
+def xeb_plan_profile(plan, enable: bool):
+    _check(load().xeb_plan_profile(plan, 1 if enable else 0))
+
+
+def xeb_plan_profile_read(plan) -> dict:
+    arrs = [np.zeros(XEB_N_KC) for _ in range(4)]
+    _check(load().xeb_plan_profile_read(plan, *[_ptr(a, ctypes.c_double) for a in arrs]))
+    out = {}
+    for c, name in enumerate(KERNEL_CLASSES):
+        if arrs[1][c] > 0:
+            out[name] = {"ms": arrs[0][c], "launches": int(arrs[1][c]), "flops": arrs[2][c], "bytes": arrs[3][c]}
+    return out
 
 
 class Plan:

@@ -74,7 +74,67 @@ struct xeb_plan_s {
     int n_xeb_blocks = 64;
     bool tables_ready = false;
     bool amps_ready = false;
+    // profiling
+    bool profiling = false;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+        double flops, bytes;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double prof_ms[XEB_N_KC] = {0}, prof_n[XEB_N_KC] = {0}, prof_flops[XEB_N_KC] = {0}, prof_bytes[XEB_N_KC] = {0};
 };
+
+namespace {
+cudaEvent_t take_event(xeb_plan_s* p) {
+    if (!p->event_pool.empty()) {
+        cudaEvent_t e = p->event_pool.back();
+        p->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one launch with events when profiling is on.
+struct ProfScope {
+    xeb_plan_s* p;
+    cudaStream_t st;
+    int cls;
+    double flops, bytes;
+    cudaEvent_t a = nullptr;
+    ProfScope(xeb_plan_s* p_, cudaStream_t st_, int cls_, double flops_, double bytes_)
+        : p(p_), st(st_), cls(cls_), flops(flops_), bytes(bytes_) {
+        if (p->profiling) {
+            a = take_event(p);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope() {
+        if (!p->profiling || !a) return;
+        cudaEvent_t b = take_event(p);
+        cudaEventRecord(b, st);
+        p->pending.push_back({cls, a, b, flops, bytes});
+    }
+};
+
+void drain_profile(xeb_plan_s* p) {
+    for (auto& r : p->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            p->prof_ms[r.cls] += ms;
+            p->prof_n[r.cls] += 1;
+            p->prof_flops[r.cls] += r.flops;
+            p->prof_bytes[r.cls] += r.bytes;
+        }
+        p->event_pool.push_back(r.a);
+        p->event_pool.push_back(r.b);
+    }
+    p->pending.clear();
+}
+}  // namespace
 
 extern "C" {
 
@@ -143,7 +203,7 @@ bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& slic
     cand.tree = tree;
     if (!analyze(net, tree, sliced, cand.an, err)) return false;
     fill_counts(cand.an, dc);
-    build_program(cand.an, cand.prog);
+    build_program(cand.an, cand.prog, o.reserved[0] == 0);
     plan_memory(cand.prog);
     cand.costs = tree_costs(cand.an, cand.prog, k);
     cand.arena_bytes = cand.prog.arena_elems * int64_t(elem);
@@ -270,6 +330,8 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
 
 extern "C" void xeb_plan_destroy(xeb_plan_s* p) {
     if (!p) return;
+    drain_profile(p);
+    for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
     if (p->owns && p->ws) cudaFree(p->ws);
     delete p;
 }
@@ -510,9 +572,17 @@ void build_launches(xeb_plan_s* p) {
             d.a_off = pr.bufs[op.a_buf].off;
             d.b_off = pr.bufs[op.b_buf].off;
             d.c_off = pr.bufs[op.c_buf].off;
-            d.sa_key = op.sa_key; d.sa_m = op.sa_m; d.sa_k = op.sa_k;
-            d.sb_key = op.sb_key; d.sb_k = op.sb_k; d.sb_n = op.sb_n;
-            d.sc_key = op.sc_key; d.sc_m = op.sc_m; d.sc_n = op.sc_n;
+            d.a_key = int64_t(1) << op.a_rank;
+            d.b_key = int64_t(1) << op.b_rank;
+            d.c_key = op.M * op.N;
+            d.nam = int(op.a_pos_m.size());
+            d.nak = int(op.a_pos_k.size());
+            d.nbk = int(op.b_pos_k.size());
+            d.nbn = int(op.b_pos_n.size());
+            for (int t = 0; t < d.nam; ++t) d.apm[t] = int8_t(op.a_pos_m[t]);
+            for (int t = 0; t < d.nak; ++t) d.apk[t] = int8_t(op.a_pos_k[t]);
+            for (int t = 0; t < d.nbk; ++t) d.bpk[t] = int8_t(op.b_pos_k[t]);
+            for (int t = 0; t < d.nbn; ++t) d.bpn[t] = int8_t(op.b_pos_n[t]);
             const int ti = p->trie_of_node[op.node];
             if (ti >= 0) {
                 const xebk::TrieDesc& t = p->trie[ti];
@@ -559,9 +629,23 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
         }
         const xebk::GemmDesc& g = p->gemms[i].d;
         const int64_t ka = an.nodes[op.a_node].kv, kb = an.nodes[op.b_node].kv;
-        const int64_t a_hi = g.a_off + (ka - 1) * g.sa_key + (g.M - 1) * g.sa_m + (g.K - 1) * g.sa_k;
-        const int64_t b_hi = g.b_off + (kb - 1) * g.sb_key + (g.K - 1) * g.sb_k + (g.N - 1) * g.sb_n;
-        const int64_t c_hi = g.c_off + (g.kv - 1) * g.sc_key + (g.M - 1) * g.sc_m + (g.N - 1) * g.sc_n;
+        auto perm_ok = [](const int8_t* a, int na, const int8_t* b, int nb, int rank) {
+            if (na + nb != rank) return false;
+            std::vector<int> seen(rank, 0);
+            for (int t = 0; t < na; ++t) { if (a[t] < 0 || a[t] >= rank) return false; ++seen[a[t]]; }
+            for (int t = 0; t < nb; ++t) { if (b[t] < 0 || b[t] >= rank) return false; ++seen[b[t]]; }
+            for (int t = 0; t < rank; ++t) if (seen[t] != 1) return false;
+            return true;
+        };
+        if (!perm_ok(g.apm, g.nam, g.apk, g.nak, op.a_rank) || !perm_ok(g.bpk, g.nbk, g.bpn, g.nbn, op.b_rank) ||
+            g.nak != g.nbk || (int64_t(1) << g.nam) != g.M || (int64_t(1) << g.nbn) != g.N ||
+            (int64_t(1) << g.nak) != g.K) {
+            why = "gemm index positions of node " + std::to_string(op.node);
+            return false;
+        }
+        const int64_t a_hi = g.a_off + ka * g.a_key - 1;
+        const int64_t b_hi = g.b_off + kb * g.b_key - 1;
+        const int64_t c_hi = g.c_off + g.kv * g.c_key - 1;
         if (!inside(op.a_buf, g.a_off, a_hi) || !inside(op.b_buf, g.b_off, b_hi) || !inside(op.c_buf, g.c_off, c_hi)) {
             why = "gemm operand of node " + std::to_string(op.node);
             return false;
@@ -590,21 +674,38 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
     XEB_CUDA(cudaMemsetAsync(acc, 0, size_t(kv_root) * 16, st));
     const int64_t n_slices = int64_t(1) << p->sliced.size();
     const auto* ldesc = reinterpret_cast<const xebk::LeafDesc*>(tables + p->t_leaf_desc);
+    const double es = double(sizeof(T));
     for (int64_t s = 0; s < n_slices; ++s) {
-        XEB_CUDA(xebk::launch_leaves<T>(ldesc, an.L, leafdata, arena, tables, s, st));
+        {
+            ProfScope ps(p, st, XEB_KC_LEAVES, 0.0, 0.0);
+            XEB_CUDA(xebk::launch_leaves<T>(ldesc, an.L, leafdata, arena, tables, s, st));
+        }
         for (size_t i = 0; i < pr.ops.size(); ++i) {
             const Op& op = pr.ops[i];
             if (op.kind == OP_PERM) {
+                ProfScope ps(p, st, XEB_KC_PERMUTE, 0.0, 2.0 * es * double(op.keys) * std::ldexp(1.0, op.r));
                 XEB_CUDA(xebk::launch_permute<T>(p->perms[i], arena + pr.bufs[op.src_buf].off,
                                                  arena + pr.bufs[op.dst_buf].off, st));
             } else {
-                XEB_CUDA(xebk::launch_gemm<T>(p->gemms[i].kernel, p->gemms[i].d, arena, st));
+                const GemmLaunch& g = p->gemms[i];
+                const double ka = double(an.nodes[op.a_node].kv), kb = double(an.nodes[op.b_node].kv);
+                const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
+                const double by = es * (ka * double(op.M * op.K) + kb * double(op.K * op.N) +
+                                        double(op.kv) * double(op.M * op.N));
+                static const int cls_of[4] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
+                                              XEB_KC_GEMM_TAIL};
+                ProfScope ps(p, st, cls_of[g.kernel], fl, by);
+                XEB_CUDA(xebk::launch_gemm<T>(g.kernel, g.d, arena, st));
             }
         }
-        XEB_CUDA(xebk::launch_root_accum<T>(arena + pr.bufs[pr.node_buf.back()].off, acc, kv_root, st));
+        {
+            ProfScope ps(p, st, XEB_KC_ACCUM, 0.0, double(kv_root) * (16.0 + 2 * es));
+            XEB_CUDA(xebk::launch_root_accum<T>(arena + pr.bufs[pr.node_buf.back()].off, acc, kv_root, st));
+        }
     }
     const int troot = p->trie_of_node[int(an.nodes.size()) - 1];
     const int32_t* key_root = reinterpret_cast<const int32_t*>(tables + p->trie[troot].key_off);
+    ProfScope ps(p, st, XEB_KC_XEB, 0.0, double(p->k) * 36.0);
     XEB_CUDA(xebk::launch_gather_xeb(acc, key_root, int64_t(p->k), amps_out,
                                      reinterpret_cast<double*>(tables + p->t_partials), p->n_xeb_blocks,
                                      reinterpret_cast<double*>(tables + p->t_result), p->net.n, st));
@@ -613,6 +714,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
 
 xeb_status build_tables(xeb_plan_s* p, cudaStream_t st) {
     char* tables = p->ws + p->off_tables;
+    ProfScope ps(p, st, XEB_KC_TRIE, 0.0, double(p->k) * 8.0 * double(p->trie.size() + 1));
     const auto* tdesc = reinterpret_cast<const xebk::TrieDesc*>(tables + p->t_trie_desc);
     XEB_CUDA(xebk::launch_trie_keys(tdesc, int(p->trie.size()), reinterpret_cast<const uint64_t*>(tables + p->t_bits),
                                     int(p->k), reinterpret_cast<const int32_t*>(tables + p->t_pi), tables,
@@ -767,5 +869,25 @@ extern "C" xeb_status xeb_plan_keys(xeb_plan_s* p, int node, int32_t* key, int32
     if (uL) XEB_CUDA(cudaMemcpyAsync(uL, tables + d.uL_off, size_t(d.kv) * 4, cudaMemcpyDeviceToHost, st));
     if (uR) XEB_CUDA(cudaMemcpyAsync(uR, tables + d.uR_off, size_t(d.kv) * 4, cudaMemcpyDeviceToHost, st));
     XEB_CUDA(cudaStreamSynchronize(st));
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_profile(xeb_plan_s* p, int enable) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    drain_profile(p);
+    for (int c = 0; c < XEB_N_KC; ++c) p->prof_ms[c] = p->prof_n[c] = p->prof_flops[c] = p->prof_bytes[c] = 0;
+    p->profiling = enable != 0;
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_profile_read(xeb_plan_s* p, double* ms, double* n, double* flops, double* bytes) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    drain_profile(p);
+    for (int c = 0; c < XEB_N_KC; ++c) {
+        if (ms) ms[c] = p->prof_ms[c];
+        if (n) n[c] = p->prof_n[c];
+        if (flops) flops[c] = p->prof_flops[c];
+        if (bytes) bytes[c] = p->prof_bytes[c];
+    }
     return XEB_OK;
 }

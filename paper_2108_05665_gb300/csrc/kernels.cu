@@ -274,8 +274,16 @@ cudaError_t launch_permute(const PermDesc& p, const T* src, T* dst, cudaStream_t
 
 // ---- a4/a5: contractions ----------------------------------------------------------
 
+// Address offset of index x whose bit i sits at address bit pos[i].
+__device__ __forceinline__ int64_t scatter(int64_t x, const int8_t* pos, int n) {
+    int64_t off = 0;
+    for (int i = 0; x != 0 && i < n; ++i, x >>= 1)
+        if (x & 1) off |= int64_t(1) << pos[i];
+    return off;
+}
+
 template <typename T>
-__global__ void k_gemm_generic(const GemmDesc g, T* __restrict__ arena) {
+__global__ void k_gemm_generic(const __grid_constant__ GemmDesc g, T* __restrict__ arena) {
     const int64_t total = g.kv * g.M * g.N;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
@@ -285,22 +293,26 @@ __global__ void k_gemm_generic(const GemmDesc g, T* __restrict__ arena) {
         const int64_t u = rest / g.M;
         const int64_t ua = g.uL ? g.uL[u] : 0;
         const int64_t ub = g.uR ? g.uR[u] : 0;
-        const T* a = arena + g.a_off + ua * g.sa_key + m * g.sa_m;
-        const T* b = arena + g.b_off + ub * g.sb_key + n * g.sb_n;
+        const T* a = arena + g.a_off + ua * g.a_key + scatter(m, g.apm, g.nam);
+        const T* b = arena + g.b_off + ub * g.b_key + scatter(n, g.bpn, g.nbn);
         T acc = czero<T>();
-        for (int64_t k = 0; k < g.K; ++k) acc = cfma(acc, a[k * g.sa_k], b[k * g.sb_k]);
-        arena[g.c_off + u * g.sc_key + m * g.sc_m + n * g.sc_n] = acc;
+        for (int64_t k = 0; k < g.K; ++k)
+            acc = cfma(acc, a[scatter(k, g.apk, g.nak)], b[scatter(k, g.bpk, g.nbk)]);
+        arena[g.c_off + u * g.c_key + m * g.N + n] = acc;
     }
 }
 
 // 64 x 64 output tile per CTA, 8-deep K slices, 256 threads with 4 x 4 each.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_tiled(const GemmDesc g, T* __restrict__ arena,
+__global__ void __launch_bounds__(256) k_gemm_tiled(const __grid_constant__ GemmDesc g, T* __restrict__ arena,
                                                     int64_t mt, int64_t nt) {
     __shared__ T As[8][64];
     __shared__ T Bs[8][64];
+    __shared__ int64_t rowA[64], colB[64], kA[8], kB[8];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
+    const bool a_along_k = g.nak > 0 && g.apk[0] == 0;
+    const bool b_along_n = g.nbn > 0 && g.bpn[0] == 0;
     const int64_t n_tiles = g.kv * mt * nt;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t u = tile % g.kv;
@@ -309,25 +321,28 @@ __global__ void __launch_bounds__(256) k_gemm_tiled(const GemmDesc g, T* __restr
         const int64_t n0 = (rest / mt) * 64;
         const int64_t ua = g.uL ? g.uL[u] : 0;
         const int64_t ub = g.uR ? g.uR[u] : 0;
-        const T* A = arena + g.a_off + ua * g.sa_key;
-        const T* B = arena + g.b_off + ub * g.sb_key;
+        const T* A = arena + g.a_off + ua * g.a_key;
+        const T* B = arena + g.b_off + ub * g.b_key;
+        if (tid < 64) rowA[tid] = m0 + tid < g.M ? scatter(m0 + tid, g.apm, g.nam) : -1;
+        else if (tid < 128) colB[tid - 64] = n0 + tid - 64 < g.N ? scatter(n0 + tid - 64, g.bpn, g.nbn) : -1;
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = czero<T>();
         for (int64_t k0 = 0; k0 < g.K; k0 += 8) {
+            if (tid < 8) kA[tid] = k0 + tid < g.K ? scatter(k0 + tid, g.apk, g.nak) : -1;
+            else if (tid < 16) kB[tid - 8] = k0 + tid - 8 < g.K ? scatter(k0 + tid - 8, g.bpk, g.nbk) : -1;
+            __syncthreads();
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 const int e = tid + r * 256;
                 int mm, kk;
-                if (g.sa_k == 1) { kk = e & 7; mm = e >> 3; } else { mm = e & 63; kk = e >> 6; }
-                const int64_t m = m0 + mm, k = k0 + kk;
-                As[kk][mm] = (m < g.M && k < g.K) ? A[m * g.sa_m + k * g.sa_k] : czero<T>();
+                if (a_along_k) { kk = e & 7; mm = e >> 3; } else { mm = e & 63; kk = e >> 6; }
+                As[kk][mm] = (rowA[mm] >= 0 && kA[kk] >= 0) ? A[rowA[mm] + kA[kk]] : czero<T>();
                 int nn, kb;
-                if (g.sb_n == 1) { nn = e & 63; kb = e >> 6; } else { kb = e & 7; nn = e >> 3; }
-                const int64_t n = n0 + nn, k2 = k0 + kb;
-                Bs[kb][nn] = (n < g.N && k2 < g.K) ? B[k2 * g.sb_k + n * g.sb_n] : czero<T>();
+                if (b_along_n) { nn = e & 63; kb = e >> 6; } else { kb = e & 7; nn = e >> 3; }
+                Bs[kb][nn] = (colB[nn] >= 0 && kB[kb] >= 0) ? B[kB[kb] + colB[nn]] : czero<T>();
             }
             __syncthreads();
 #pragma unroll
@@ -344,7 +359,7 @@ __global__ void __launch_bounds__(256) k_gemm_tiled(const GemmDesc g, T* __restr
             }
             __syncthreads();
         }
-        T* C = arena + g.c_off + u * g.sc_key;
+        T* C = arena + g.c_off + u * g.c_key;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int64_t m = m0 + ty * 4 + i;
@@ -352,16 +367,26 @@ __global__ void __launch_bounds__(256) k_gemm_tiled(const GemmDesc g, T* __restr
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t n = n0 + tx * 4 + j;
-                if (n < g.N) C[m * g.sc_m + n * g.sc_n] = acc[i][j];
+                if (n < g.N) C[m * g.N + n] = acc[i][j];
             }
         }
+        __syncthreads();
     }
 }
 
 // N == 1: one thread per (left-key group, row m); the A row is shared by all
 // keys of the group (keys are sorted by their left key, so groups are runs).
+constexpr int kGemvK = 256;
 template <typename T>
-__global__ void k_gemm_gemv(const GemmDesc g, T* __restrict__ arena) {
+__global__ void k_gemm_gemv(const __grid_constant__ GemmDesc g, T* __restrict__ arena) {
+    __shared__ int64_t kA[kGemvK], kB[kGemvK];
+    const bool table = g.K <= kGemvK;
+    if (table)
+        for (int k = threadIdx.x; k < g.K; k += blockDim.x) {
+            kA[k] = scatter(k, g.apk, g.nak);
+            kB[k] = scatter(k, g.bpk, g.nbk);
+        }
+    __syncthreads();
     const int64_t total = g.n_groups * g.M;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
@@ -369,32 +394,39 @@ __global__ void k_gemm_gemv(const GemmDesc g, T* __restrict__ arena) {
         const int64_t grp = e / g.M;
         const int64_t u0 = g.gstart ? g.gstart[grp] : 0;
         const int64_t u1 = g.gstart ? g.gstart[grp + 1] : g.kv;
+        if (u1 <= u0) continue;
         const int64_t ua = g.uL ? g.uL[u0] : 0;
-        const T* a = arena + g.a_off + ua * g.sa_key + m * g.sa_m;
+        const T* a = arena + g.a_off + ua * g.a_key + scatter(m, g.apm, g.nam);
         for (int64_t u = u0; u < u1; ++u) {
             const int64_t ub = g.uR ? g.uR[u] : 0;
-            const T* b = arena + g.b_off + ub * g.sb_key;
+            const T* b = arena + g.b_off + ub * g.b_key;
             T acc = czero<T>();
-            for (int64_t k = 0; k < g.K; ++k) acc = cfma(acc, a[k * g.sa_k], b[k * g.sb_k]);
-            arena[g.c_off + u * g.sc_key + m * g.sc_m] = acc;
+            if (table) {
+                for (int64_t k = 0; k < g.K; ++k) acc = cfma(acc, a[kA[k]], b[kB[k]]);
+            } else {
+                for (int64_t k = 0; k < g.K; ++k)
+                    acc = cfma(acc, a[scatter(k, g.apk, g.nak)], b[scatter(k, g.bpk, g.nbk)]);
+            }
+            arena[g.c_off + u * g.c_key + m] = acc;
         }
     }
 }
 
 // M == N == 1: a warp per key, lanes split K, shuffle reduction.
 template <typename T>
-__global__ void k_gemm_tail(const GemmDesc g, T* __restrict__ arena) {
+__global__ void k_gemm_tail(const __grid_constant__ GemmDesc g, T* __restrict__ arena) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t u = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; u < g.kv; u += warps) {
         const int64_t ua = g.uL ? g.uL[u] : 0;
         const int64_t ub = g.uR ? g.uR[u] : 0;
-        const T* a = arena + g.a_off + ua * g.sa_key;
-        const T* b = arena + g.b_off + ub * g.sb_key;
+        const T* a = arena + g.a_off + ua * g.a_key;
+        const T* b = arena + g.b_off + ub * g.b_key;
         T acc = czero<T>();
-        for (int64_t k = lane; k < g.K; k += 32) acc = cfma(acc, a[k * g.sa_k], b[k * g.sb_k]);
+        for (int64_t k = lane; k < g.K; k += 32)
+            acc = cfma(acc, a[scatter(k, g.apk, g.nak)], b[scatter(k, g.bpk, g.nbk)]);
         for (int d = 16; d > 0; d >>= 1) acc = cadd(acc, shfl_down(acc, d));
-        if (lane == 0) arena[g.c_off + u * g.sc_key] = acc;
+        if (lane == 0) arena[g.c_off + u * g.c_key] = acc;
     }
 }
 

@@ -52,13 +52,17 @@ struct PermDesc {
 };
 
 // One pairwise contraction, for u < kv: C_u = A_{uL(u)} (M x K) * B_{uR(u)} (K x N).
+// Operands are read in place: bit i of the row index m sits at address bit
+// apm[i] of A's tensor, bit i of the summed index k at apk[i] (A) / bpk[i] (B),
+// bit i of the column index n at bpn[i] (B).  C is written row-major [M][N].
+constexpr int kMaxLegs = 48;
 struct GemmDesc {
     int64_t M, N, K, kv;
-    int64_t a_off, sa_key, sa_m, sa_k;
-    int64_t b_off, sb_key, sb_k, sb_n;
-    int64_t c_off, sc_key, sc_m, sc_n;
-    const int32_t* uL;   // nullptr -> 0
-    const int32_t* uR;   // nullptr -> 0
+    int64_t a_off, a_key, b_off, b_key, c_off, c_key;
+    int nam, nak, nbk, nbn;
+    int8_t apm[kMaxLegs], apk[kMaxLegs], bpk[kMaxLegs], bpn[kMaxLegs];
+    const int32_t* uL;      // nullptr -> 0
+    const int32_t* uR;      // nullptr -> 0
     const int32_t* gstart;  // groups of keys by uL (nullptr -> one group)
     int64_t n_groups;
 };

@@ -297,7 +297,7 @@ std::vector<int> concat(const std::vector<int>& a, const std::vector<int>& b) {
 }
 }  // namespace
 
-void build_program(const Analysis& an, Program& prog) {
+void build_program(const Analysis& an, Program& prog, bool gather) {
     const int N = int(an.nodes.size());
     const int L = an.L;
     int n_legs = 0;
@@ -315,8 +315,18 @@ void build_program(const Analysis& an, Program& prog) {
         return int(prog.bufs.size()) - 1;
     };
     auto elems_of = [&](int v) { return an.nodes[v].kv * (int64_t(1) << an.nodes[v].legs.size()); };
+    // leaves are materialised in their canonical leg order
+    for (int j = 0; j < L; ++j) {
+        prog.layout[j] = an.nodes[j].legs;
+        prog.node_buf[j] = new_buf(elems_of(j), 0);
+    }
     std::vector<char> inS(std::max(n_legs, 1), 0);
     std::vector<int> s1, f1, s2, f2;
+    // address bit of `leg` in layout `lay` (slowest first)
+    auto pos_of = [](const std::vector<int>& lay, int leg) {
+        const int i = int(std::find(lay.begin(), lay.end(), leg) - lay.begin());
+        return int(lay.size()) - 1 - i;
+    };
     for (int v = L; v < N; ++v) {
         const Node& nd = an.nodes[v];
         const int c1 = nd.l, c2 = nd.r;
@@ -326,11 +336,6 @@ void build_program(const Analysis& an, Program& prog) {
             if (inS[l]) S.push_back(l);
         for (int l : an.nodes[c2].legs) inS[l] = 0;
         for (int l : S) inS[l] = 1;
-        const bool leaf1 = c1 < L, leaf2 = c2 < L;
-        int k1 = -1, k2 = -1;
-        if (!leaf1) k1 = split_kind(prog.layout[c1], inS, s1, f1);
-        if (!leaf2) k2 = split_kind(prog.layout[c2], inS, s2, f2);
-        const int op_index = int(prog.ops.size()) + 1;  // op 0 = leaf materialisation
         auto permute_to = [&](int c, const std::vector<int>& lay) {
             Op op;
             op.kind = OP_PERM;
@@ -340,11 +345,7 @@ void build_program(const Analysis& an, Program& prog) {
             op.keys = an.nodes[c].kv;
             const std::vector<int>& old = prog.layout[c];
             op.perm.assign(op.r, 0);
-            for (int j = 0; j < op.r; ++j) {
-                const int leg = lay[op.r - 1 - j];
-                const int pos = int(std::find(old.begin(), old.end(), leg) - old.begin());
-                op.perm[j] = op.r - 1 - pos;
-            }
+            for (int j = 0; j < op.r; ++j) op.perm[j] = pos_of(old, lay[op.r - 1 - j]);
             const int idx = int(prog.ops.size()) + 1;
             op.dst_buf = new_buf(elems_of(c), idx);
             prog.bufs[op.src_buf].last = std::max(prog.bufs[op.src_buf].last, idx);
@@ -353,17 +354,9 @@ void build_program(const Analysis& an, Program& prog) {
             prog.permute_elems += 2.0 * double(elems_of(c));
             prog.ops.push_back(op);
         };
-        auto leaf_layout = [&](int c, const std::vector<int>& lay) {
-            prog.layout[c] = lay;
-            prog.node_buf[c] = new_buf(elems_of(c), 0);
-        };
-        auto free_of = [&](int c) {
-            std::vector<int> F;
-            for (int l : an.nodes[c].legs)
-                if (!inS[l]) F.push_back(l);
-            return F;
-        };
-        if (!leaf1 && !leaf2) {
+        if (!gather) {
+            const int k1 = split_kind(prog.layout[c1], inS, s1, f1);
+            const int k2 = split_kind(prog.layout[c2], inS, s2, f2);
             if (k1 >= 0 && k2 >= 0) {
                 if (s1 != s2) {
                     if (elems_of(c1) <= elems_of(c2))
@@ -380,23 +373,9 @@ void build_program(const Analysis& an, Program& prog) {
                 permute_to(c1, concat(f1, sig));
                 permute_to(c2, concat(sig, f2));
             }
-        } else if (leaf1 && !leaf2) {
-            if (k2 < 0) permute_to(c2, concat(s2, f2));
-            split_kind(prog.layout[c2], inS, s2, f2);
-            leaf_layout(c1, concat(free_of(c1), s2));
-        } else if (!leaf1 && leaf2) {
-            if (k1 < 0) permute_to(c1, concat(f1, s1));
-            split_kind(prog.layout[c1], inS, s1, f1);
-            leaf_layout(c2, concat(s1, free_of(c2)));
-        } else {
-            std::vector<int> sig(S);
-            std::sort(sig.begin(), sig.end());
-            leaf_layout(c1, concat(free_of(c1), sig));
-            leaf_layout(c2, concat(sig, free_of(c2)));
         }
-        // final operand layouts
-        const int ka = split_kind(prog.layout[c1], inS, s1, f1);
-        const int kb = split_kind(prog.layout[c2], inS, s2, f2);
+        const std::vector<int>& la = prog.layout[c1];
+        const std::vector<int>& lb = prog.layout[c2];
         Op op;
         op.kind = OP_GEMM;
         op.node = v;
@@ -404,26 +383,38 @@ void build_program(const Analysis& an, Program& prog) {
         op.b_node = c2;
         op.a_buf = prog.node_buf[c1];
         op.b_buf = prog.node_buf[c2];
-        op.M = int64_t(1) << f1.size();
-        op.N = int64_t(1) << f2.size();
-        op.K = int64_t(1) << S.size();
+        op.a_rank = int(la.size());
+        op.b_rank = int(lb.size());
+        // rows: A's free legs in ascending address order; summed index: the
+        // shared legs in ascending A address order; columns: B's free legs in
+        // ascending B address order
+        std::vector<int> fa, fb, sg;
+        for (int b = 0; b < op.a_rank; ++b) {
+            const int leg = la[op.a_rank - 1 - b];
+            if (inS[leg]) { sg.push_back(leg); op.a_pos_k.push_back(b); }
+            else { fa.push_back(leg); op.a_pos_m.push_back(b); }
+        }
+        for (int leg : sg) op.b_pos_k.push_back(pos_of(lb, leg));
+        for (int b = 0; b < op.b_rank; ++b) {
+            const int leg = lb[op.b_rank - 1 - b];
+            if (!inS[leg]) { fb.push_back(leg); op.b_pos_n.push_back(b); }
+        }
+        op.M = int64_t(1) << fa.size();
+        op.N = int64_t(1) << fb.size();
+        op.K = int64_t(1) << sg.size();
         op.kv = nd.kv;
-        op.sa_key = op.M * op.K;
-        if (ka == 0) { op.sa_m = op.K; op.sa_k = 1; } else { op.sa_m = 1; op.sa_k = op.M; }
-        op.sb_key = op.K * op.N;
-        if (kb == 1 || f2.empty()) { op.sb_k = op.N; op.sb_n = 1; } else { op.sb_k = 1; op.sb_n = op.K; }
-        if (f1.empty()) { op.sa_m = op.K; op.sa_k = 1; }
-        if (S.empty()) { op.sa_k = 0; op.sb_k = 0; }
-        op.sc_key = op.M * op.N;
-        op.sc_m = op.N;
-        op.sc_n = 1;
         const int idx = int(prog.ops.size()) + 1;
-        (void)op_index;
         op.c_buf = new_buf(elems_of(v), idx);
         prog.bufs[op.a_buf].last = std::max(prog.bufs[op.a_buf].last, idx);
         prog.bufs[op.b_buf].last = std::max(prog.bufs[op.b_buf].last, idx);
         prog.node_buf[v] = op.c_buf;
-        prog.layout[v] = concat(f1, f2);
+        // C = [rows][cols] row-major: slowest-first layout is the reverse of
+        // the ascending address order
+        std::vector<int> lay;
+        for (size_t t = fa.size(); t-- > 0;) lay.push_back(fa[t]);
+        std::vector<int> lc;
+        for (size_t t = fb.size(); t-- > 0;) lc.push_back(fb[t]);
+        prog.layout[v] = concat(lay, lc);
         prog.ops.push_back(op);
         for (int l : S) inS[l] = 0;
     }

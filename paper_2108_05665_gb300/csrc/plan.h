@@ -79,9 +79,10 @@ struct Op {
     int a_buf = -1, b_buf = -1, c_buf = -1;
     int a_node = -1, b_node = -1;
     int64_t M = 1, N = 1, K = 1, kv = 1;
-    int64_t sa_key = 0, sa_m = 0, sa_k = 0;
-    int64_t sb_key = 0, sb_k = 0, sb_n = 0;
-    int64_t sc_key = 0, sc_m = 0, sc_n = 0;
+    // operand addressing: bit i of the row / summed / column index sits at
+    // address bit pos[i] of the operand tensor (legs have dimension 2)
+    std::vector<int> a_pos_m, a_pos_k, b_pos_k, b_pos_n;
+    int a_rank = 0, b_rank = 0;
 };
 
 struct Buffer {
@@ -99,7 +100,10 @@ struct Program {
     double permute_elems = 0;
 };
 
-void build_program(const Analysis& an, Program& prog);
+// gather = true: contractions read their operands in place through per-leg
+// address positions (no permutation passes); false: permute operands into
+// [free][summed] blocks first.
+void build_program(const Analysis& an, Program& prog, bool gather);
 void plan_memory(Program& prog);  // emulation-mode allocator: exact arena peak
 
 struct Costs {

@@ -1,0 +1,34 @@
+"""Full-size parity on the 5x6-grid, 14-cycle, 10,000-bitstring workload (the
+benchmark's), in the launch configuration bench.py times: every amplitude
+against the FP64 state-vector oracle values stored by
+tests/golden/make_grid5x6_fixture.py, and F against the oracle's F."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2108_05665_gb300 import binding as B, build, inputs
+from gpu_util import rel_err, run
+
+pytestmark = pytest.mark.gpu
+
+FIX = os.path.join(os.path.dirname(__file__), "golden", "grid5x6_m14_k10000.npz")
+
+
+@pytest.fixture(scope="module")
+def fixture():
+    build.build()
+    z = np.load(FIX)
+    w = inputs.WORKLOADS["grid5x6_m14_k10000"]
+    return w.circuit(), np.asarray(z["bitstrings"], dtype=np.uint64), z["amplitudes"], float(z["F"])
+
+
+@pytest.mark.parametrize("precision", [B.XEB_PREC_FP32])
+def test_grid5x6_all_amplitudes(fixture, precision):
+    circ, bits, ref, F_ref = fixture
+    amps, F, plan = run(circ, bits, precision=precision)
+    err = rel_err(amps, ref, circ.n_qubits)
+    print("max rel err %.3e  median %.3e  |dF| %.3e" % (err.max(), np.median(err), abs(F - F_ref)))
+    assert err.max() < 1e-5
+    assert abs(F - F_ref) < 1e-6
+    plan.close()

@@ -125,7 +125,7 @@ def test_worked_example_circuit():
     circ = inputs.Circuit(3, gates)
     bits = np.array([0, 1, 7, 4, 5, 2], dtype=np.uint64)
     closed = np.array([(1 if (b >> 2) & 1 == 0 else (-1) ** ((b & 1) + ((b >> 1) & 1))) / (2 * math.sqrt(2))
-                       for b in bits])
+                       for b in (int(x) for x in bits)])
     amps, F, plan = run(circ, bits, precision=B.XEB_PREC_FP64)
     assert np.abs(amps - closed).max() < 1e-15
     plan.close()

@@ -52,3 +52,19 @@ def test_xeb_closed_forms():
     # duplicates count every time (sum over the sequence)
     b = np.array([1.0, 0.0, 0.0, 0.0], dtype=np.complex128)
     assert xeb.fidelity(b, 2) == 0.0
+
+
+def test_grid5x6_fixture_consistent():
+    """The stored oracle values of the benchmark workload obey Eq. (1) and
+    the statistics: half ideal samples, half uniform -> F ~ (2^n sum p^2 - 1)/2."""
+    import os
+    z = np.load(os.path.join(os.path.dirname(__file__), "golden", "grid5x6_m14_k10000.npz"))
+    n, k = 30, len(z["bitstrings"])
+    assert k == 10000
+    assert abs(xeb.fidelity(z["amplitudes"], n) - float(z["F"])) < 1e-12
+    assert abs(float(z["norm"]) - 1) < 1e-10
+    assert abs(float(z["collision"]) - 2) < 0.01
+    assert abs(float(z["F"]) - (float(z["collision"]) - 1) / 2) < 5 * math.sqrt(2 / k)
+    uni = z["bitstrings"][5000:]
+    w = inputs.WORKLOADS["grid5x6_m14_k10000"]
+    assert np.array_equal(uni, inputs.uniform_bitstrings(n, 5000, w.bitstring_seed))
