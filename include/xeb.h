@@ -104,7 +104,9 @@ typedef struct {
     int planner;          /* XEB_PLANNER_*                                       */
     int block_qubits;     /* sweep planner: max qubits per body block (0 = try)  */
     int group_leaves;     /* sweep planner: output leaves per trie level (0=try) */
-    double alpha;         /* objective: arithmetic intensity (0 = from precision) */
+    double alpha;         /* objective: arithmetic intensity alpha of
+                             log2(C + alpha RW); 0 = use log2 of a time
+                             estimate from a GB300 efficiency profile instead */
     double beta;          /* objective: memory penalty factor                    */
     uint64_t mem_budget;  /* M_max in bytes for the contraction arena            */
     uint64_t seed;        /* planner randomisation                               */
@@ -209,6 +211,7 @@ enum {
     XEB_KC_ACCUM = 7,         /* a6 FP64 accumulation over slices                */
     XEB_KC_XEB = 8,           /* a7 gather + linear XEB                          */
     XEB_KC_GEMM_TC = 9,       /* a4 tcgen05 split-precision complex GEMM         */
+    XEB_KC_GEMM_STREAM = 10,  /* a4 memory-bound streaming contraction (SIMT)    */
     XEB_N_KC = 16
 };
 

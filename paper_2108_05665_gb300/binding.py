@@ -251,7 +251,7 @@ def xeb_plan_keys(plan, node: int, k: int, kv: int, stream: int):
 
 
 KERNEL_CLASSES = ["trie", "leaves", "permute", "gemm_tiled", "gemm_gemv", "gemm_tail", "gemm_generic",
-                  "accum", "xeb", "gemm_tc"]
+                  "accum", "xeb", "gemm_tc", "gemm_stream"]
 XEB_N_KC = 16
 
 

@@ -32,10 +32,88 @@ xeb_status fail(xeb_status s, const std::string& msg) {
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+constexpr int GK_TC = 100;  // tcgen05 split-precision kernel (tc_gemm.cu)
+
 struct GemmLaunch {
     int kernel;
     xebk::GemmDesc d;
+    xebk::StreamDesc s;
+    xebk::TcDesc tc;
 };
+
+// Tensor-core eligibility and descriptor of a contraction (one key, 128-row
+// tiles, 16 <= K, N <= 64 complex, tile offsets within 32 bits).
+bool tc_tile(const Op& op, xebk::TcDesc& t) {
+    if (!tc_eligible(op)) return false;
+    if (op.a_pos_m.size() > size_t(xebk::kMaxLegs)) return false;
+    std::memset(&t, 0, sizeof(t));
+    t.M = op.M;
+    t.K2 = int(2 * op.K);
+    t.N2 = int(2 * op.N);
+    t.n_chunks = t.K2 / 32;
+    t.tmem_cols = 4 * t.N2;  // 2 buffers x (big, small) accumulators
+    std::vector<std::pair<int, int>> bits;
+    for (int i = 0; i < 7; ++i) bits.push_back({op.a_pos_m[i], 0});
+    for (int i = 0; i < 4; ++i) bits.push_back({op.a_pos_k[i], 1});
+    std::sort(bits.begin(), bits.end());
+    for (auto& b : bits)
+        if (b.first > 30) return false;
+    t.T = int(bits.size());
+    for (int i = 0; i < t.T; ++i) {
+        t.pos[i] = int8_t(bits[i].first);
+        if (bits[i].second) t.is_k |= 1u << i;
+    }
+    for (int c = 0; c < t.n_chunks; ++c) {
+        int64_t o = 0;
+        for (size_t i = 4; i < op.a_pos_k.size(); ++i)
+            if ((c >> (i - 4)) & 1) o |= int64_t(1) << op.a_pos_k[i];
+        if (o > INT32_MAX) return false;
+        t.chunk_off[c] = int32_t(o);
+    }
+    t.nam = int(op.a_pos_m.size());
+    for (int i = 0; i < t.nam; ++i) t.apm[i] = int8_t(op.a_pos_m[i]);
+    t.nbk = int(op.b_pos_k.size());
+    t.nbn = int(op.b_pos_n.size());
+    for (int i = 0; i < t.nbk; ++i) t.bpk[i] = int8_t(op.b_pos_k[i]);
+    for (int i = 0; i < t.nbn; ++i) t.bpn[i] = int8_t(op.b_pos_n[i]);
+    return true;
+}
+
+// Tile shape of the streaming kernel for a contraction, or false if the
+// contraction does not fit it.
+bool stream_tile(const Op& op, size_t elem, xebk::StreamDesc& s) {
+    if (op.K > xebk::kStreamMaxK || op.N > xebk::kStreamMaxN || op.M < 64) return false;
+    const int npt = op.N <= 8 ? int(op.N) : (op.N == 16 ? 8 : 16);
+    const int tpr = int(op.N) >= npt ? int(op.N) / npt : 1;
+    const int rg = 256 / tpr;
+    int R = 1;
+    while (2 * R <= op.M && 2 * R * op.K <= 256 * xebk::kStreamEPT && 2 * R <= rg * std::max(1, 16 / npt) &&
+           size_t(2 * R) * size_t(op.K) * elem <= 32 * 1024)
+        R *= 2;
+    if (R < 32 || R * op.K > 256 * xebk::kStreamEPT) return false;
+    int tm = 0;
+    while ((1 << tm) < R) ++tm;
+    for (int q : op.a_pos_k)
+        if (q > 30) return false;  // tile offsets are 32-bit
+    for (int i = 0; i < tm; ++i)
+        if (op.a_pos_m[i] > 30) return false;
+    // tile bits: the tm lowest row bits and all summed bits, ascending address
+    std::vector<std::pair<int, int>> bits;  // (address position, is_k)
+    for (int i = 0; i < tm; ++i) bits.push_back({op.a_pos_m[i], 0});
+    for (int p : op.a_pos_k) bits.push_back({p, 1});
+    std::sort(bits.begin(), bits.end());
+    if (bits.size() > 32) return false;
+    s.R = R;
+    s.tm = tm;
+    s.T = int(bits.size());
+    s.npt = npt;
+    s.is_k = 0;
+    for (int i = 0; i < s.T; ++i) {
+        s.pos[i] = int8_t(bits[i].first);
+        if (bits[i].second) s.is_k |= 1u << i;
+    }
+    return true;
+}
 }  // namespace
 
 struct xeb_plan_s {
@@ -60,7 +138,8 @@ struct xeb_plan_s {
     size_t bytes_total = 0;
     // offsets inside tables (bytes)
     int64_t t_trie_desc = 0, t_internal = 0, t_leaf_desc = 0, t_pi = 0, t_bits = 0, t_acc = 0, t_amps = 0,
-            t_partials = 0, t_result = 0, t_err = 0;
+            t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0;
+    int n_sms = 152;
     int64_t tables_bytes = 0;
     std::vector<xebk::TrieDesc> trie;
     std::vector<int> trie_of_node;  // node -> index in trie, -1 if no bits
@@ -178,17 +257,6 @@ xeb_status xeb_network_leaves(const xeb_circuit* c, int32_t* out_bits, int32_t* 
 
 namespace {
 
-double default_alpha(int prec) {
-    // complex multiply-adds per element moved at which compute and HBM time
-    // balance on GB300 (FP32 CUDA cores ~10 T cMAC/s, 3xTF32 tensor cores
-    // ~40 T cMAC/s, HBM ~0.84 T complex64 elements/s)
-    switch (prec) {
-        case XEB_PREC_TF32X3: return 48.0;
-        case XEB_PREC_FP64: return 1.0;
-        default: return 12.0;
-    }
-}
-
 struct Candidate {
     Tree tree;
     Analysis an;
@@ -207,11 +275,16 @@ bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& slic
     plan_memory(cand.prog);
     cand.costs = tree_costs(cand.an, cand.prog, k);
     cand.arena_bytes = cand.prog.arena_elems * int64_t(elem);
-    const double alpha = o.alpha > 0 ? o.alpha : default_alpha(o.precision);
     const double budget = double(std::max<uint64_t>(o.mem_budget, 1));
     const double nsl = std::ldexp(1.0, int(sliced.size()));
-    cand.f = o.beta * std::max(std::log2(double(cand.arena_bytes) / budget), 0.0) +
-             std::log2(nsl * (cand.costs.C + alpha * (cand.costs.RW + cand.costs.perm)) + 1.0);
+    const double mem_term = o.beta * std::max(std::log2(double(cand.arena_bytes) / budget), 0.0);
+    if (o.alpha > 0) {
+        // App. A objective with arithmetic intensity alpha
+        cand.f = mem_term + std::log2(nsl * (cand.costs.C + o.alpha * (cand.costs.RW + cand.costs.perm)) + 1.0);
+    } else {
+        // efficiency-profile variant: log2 of the estimated time (seconds)
+        cand.f = mem_term + std::log2(nsl * estimate_time(cand.an, cand.prog, o.precision, elem));
+    }
     return true;
 }
 
@@ -466,6 +539,7 @@ void layout_device(xeb_plan_s* p) {
     p->t_partials = take(int64_t(p->n_xeb_blocks) * 16);
     p->t_result = take(64);
     p->t_err = take(16);
+    p->t_wimg = take(p->opts.precision == XEB_PREC_TF32X3 ? 2 * 4 * 128 * 32 * 4 : 16);
     p->tables_bytes = t;
     p->bytes_total = size_t(off + t);
 }
@@ -595,6 +669,14 @@ void build_launches(xeb_plan_s* p) {
                 d.n_groups = 1;
             }
             if (op.M == 1 && op.N == 1) g.kernel = xebk::GK_TAIL;
+            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc)) {
+                g.kernel = GK_TC;
+                g.tc.a_off = d.a_off;
+                g.tc.b_off = d.b_off;
+                g.tc.c_off = d.c_off;
+                g.tc.wimg = reinterpret_cast<float*>(tables + p->t_wimg);
+                g.tc.err = reinterpret_cast<int32_t*>(tables + p->t_err);
+            } else if (stream_tile(op, p->elem, g.s)) g.kernel = xebk::GK_STREAM;
             else if (op.N == 1) g.kernel = xebk::GK_GEMV;
             else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;
             else g.kernel = xebk::GK_GENERIC;
@@ -651,6 +733,37 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             return false;
         }
         if ((ka > 1 || kb > 1) && !g.uL) { why = "gemm without key tables"; return false; }
+        if (p->gemms[i].kernel == GK_TC) {
+            const xebk::TcDesc& t = p->gemms[i].tc;
+            if (t.M != g.M || t.M % 128 != 0 || t.K2 != 2 * g.K || t.N2 != 2 * g.N || t.K2 % 32 != 0 ||
+                t.N2 % 32 != 0 || t.N2 > 128 || t.n_chunks * 32 != t.K2 || t.n_chunks > 4 || t.T != 11 ||
+                g.kv != 1 || xebk::tc_wimg_floats(t) * 4 > size_t(2 * 4 * 128 * 32 * 4)) {
+                why = "tensor-core tile of node " + std::to_string(op.node);
+                return false;
+            }
+            // largest element a loader can touch
+            int64_t hi = 0;
+            for (int i = 0; i < t.T; ++i) hi |= int64_t(1) << t.pos[i];
+            hi += t.chunk_off[t.n_chunks - 1];
+            int64_t rowhi = 0;
+            for (int i = 7; i < t.nam; ++i) rowhi |= int64_t(1) << t.apm[i];
+            if (!inside(op.a_buf, t.a_off, t.a_off + rowhi + hi) || !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1)) {
+                why = "tensor-core operand of node " + std::to_string(op.node);
+                return false;
+            }
+            for (int i = 0; i < t.T; ++i)
+                if (t.pos[i] < 0 || t.pos[i] >= op.a_rank) { why = "tensor-core tile positions"; return false; }
+        }
+        if (p->gemms[i].kernel == xebk::GK_STREAM) {
+            const xebk::StreamDesc& sd = p->gemms[i].s;
+            if (sd.T > 32 || sd.T != sd.tm + g.nak || (1 << sd.tm) != sd.R || sd.R > g.M || sd.R < 1) {
+                why = "stream tile of node " + std::to_string(op.node);
+                return false;
+            }
+            for (int t = 0; t < sd.T; ++t)
+                if (sd.pos[t] < 0 || sd.pos[t] >= op.a_rank) { why = "stream tile positions"; return false; }
+            if (sd.tm > g.nam) { why = "stream tile rows"; return false; }
+        }
     }
     for (size_t j = 0; j < p->leafdesc.size(); ++j) {
         const xebk::LeafDesc& d = p->leafdesc[j];
@@ -692,10 +805,17 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
                 const double by = es * (ka * double(op.M * op.K) + kb * double(op.K * op.N) +
                                         double(op.kv) * double(op.M * op.N));
-                static const int cls_of[4] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
-                                              XEB_KC_GEMM_TAIL};
-                ProfScope ps(p, st, cls_of[g.kernel], fl, by);
-                XEB_CUDA(xebk::launch_gemm<T>(g.kernel, g.d, arena, st));
+                static const int cls_of[5] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
+                                              XEB_KC_GEMM_TAIL, XEB_KC_GEMM_STREAM};
+                ProfScope ps(p, st, g.kernel == GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by);
+                if (g.kernel == GK_TC) {
+                    if constexpr (sizeof(T) == 8)
+                        XEB_CUDA(xebk::launch_tc_gemm(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st));
+                } else if (g.kernel == xebk::GK_STREAM) {
+                    XEB_CUDA(xebk::launch_gemm_stream<T>(g.d, g.s, arena, st));
+                } else {
+                    XEB_CUDA(xebk::launch_gemm<T>(g.kernel, g.d, arena, st));
+                }
             }
         }
         {
@@ -742,9 +862,20 @@ extern "C" size_t xeb_plan_device_bytes(xeb_plan_s* p) {
 extern "C" xeb_status xeb_plan_bind(xeb_plan_s* p, void* workspace, size_t bytes, uintptr_t stream) {
     if (!p) return fail(XEB_EINVAL, "NULL plan");
     if (p->bound) return fail(XEB_EINVAL, "plan already bound");
-    if (p->opts.precision == XEB_PREC_TF32X3)
-        return fail(XEB_EUNSUPPORTED, "TF32x3 tensor-core contraction not built yet");
     layout_device(p);
+    {
+        int dev = 0, sms = 0;
+        XEB_CUDA(cudaGetDevice(&dev));
+        XEB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        p->n_sms = sms > 0 ? sms : 152;
+        if (p->opts.precision == XEB_PREC_TF32X3) {
+            int major = 0, minor = 0;
+            XEB_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+            XEB_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+            if (major != 10 || minor != 3)
+                return fail(XEB_EUNSUPPORTED, "TF32x3 tensor-core path is built for sm_103a only");
+        }
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (workspace) {
         if (bytes < p->bytes_total) return fail(XEB_ENOMEM, "workspace smaller than xeb_plan_device_bytes()");
@@ -824,6 +955,8 @@ extern "C" xeb_status xeb_fidelity(xeb_plan_s* p, double* F, double* m1, double*
     XEB_CUDA(cudaMemcpyAsync(res, tables + p->t_result, 32, cudaMemcpyDeviceToHost, st));
     XEB_CUDA(cudaMemcpyAsync(&err, tables + p->t_err, 4, cudaMemcpyDeviceToHost, st));
     XEB_CUDA(cudaStreamSynchronize(st));
+    if (err & xebk::kErrTimeout)
+        return fail(XEB_ETIMEOUT, "a bounded device wait gave up (role " + std::to_string(err & 0xff) + ")");
     if (err) return fail(XEB_EDEVICE, "device key tables disagree with the plan's counts (node " +
                                            std::to_string(err - 1) + ")");
     if (F) *F = res[0];

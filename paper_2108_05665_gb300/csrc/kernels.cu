@@ -451,6 +451,192 @@ cudaError_t launch_gemm(int kernel, const GemmDesc& g, T* arena, cudaStream_t st
     return cudaGetLastError();
 }
 
+// Memory-bound contraction (M large, K and N <= 64): a CTA loads R rows x all
+// K of A as contiguous address runs, transposes them in shared memory, then
+// every key of the left-key group multiplies the tile by its B and writes R x N
+// contiguous outputs.  Each thread owns one row and NPT consecutive columns.
+// The tile geometry is the same for every tile, so each thread computes the
+// address offsets and shared-memory slots of its EPT tile elements once.
+template <int NPT>
+__device__ __forceinline__ void load_vec(const float2* p, float2* out) {
+    if constexpr (NPT % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < NPT; j += 2) {
+            const float4 q = *reinterpret_cast<const float4*>(p + j);
+            out[j] = make_float2(q.x, q.y);
+            out[j + 1] = make_float2(q.z, q.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) out[j] = p[j];
+    }
+}
+template <int NPT>
+__device__ __forceinline__ void load_vec(const double2* p, double2* out) {
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) out[j] = p[j];
+}
+template <int NPT>
+__device__ __forceinline__ void store_vec(float2* p, const float2* v) {
+    if constexpr (NPT % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < NPT; j += 2)
+            *reinterpret_cast<float4*>(p + j) = make_float4(v[j].x, v[j].y, v[j + 1].x, v[j + 1].y);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) p[j] = v[j];
+    }
+}
+template <int NPT>
+__device__ __forceinline__ void store_vec(double2* p, const double2* v) {
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) p[j] = v[j];
+}
+
+__device__ __forceinline__ void cp_async_el(float2* smem, const float2* gmem) {
+    const unsigned sa = unsigned(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_el(double2* smem, const double2* gmem) {
+    const unsigned sa = unsigned(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T, int NPT>
+__global__ void __launch_bounds__(256, 2) k_gemm_stream(const __grid_constant__ GemmDesc g,
+                                                        const __grid_constant__ StreamDesc s,
+                                                        T* __restrict__ arena) {
+    extern __shared__ __align__(16) unsigned char sm_stream[];
+    const int R = s.R, K = int(g.K), N = int(g.N);
+    const int ldA = R + 1, ldB = N + (NPT > 1 ? 2 : 1);
+    const int a_sz = (K * ldA + 1) & ~1;
+    T* buf0 = reinterpret_cast<T*>(sm_stream);  // two A tiles [K][R+1], then B [K][ldB]
+    T* buf1 = buf0 + a_sz;
+    T* Bs = buf1 + a_sz;
+    const int tid = threadIdx.x;
+    const int tile_elems = R * K;
+    int32_t off[kStreamEPT];
+    int slot[kStreamEPT];
+#pragma unroll
+    for (int j = 0; j < kStreamEPT; ++j) {
+        const int e = tid + j * 256;
+        off[j] = 0;
+        slot[j] = -1;
+        if (e < tile_elems) {
+            int r = 0, k = 0, ri = 0, ki = 0;
+            int32_t o = 0;
+            for (int i = 0; i < s.T; ++i) {
+                const int bit = (e >> i) & 1;
+                if ((s.is_k >> i) & 1) k |= bit << ki++;
+                else r |= bit << ri++;
+                if (bit) o |= int32_t(1) << s.pos[i];
+            }
+            off[j] = o;
+            slot[j] = k * ldA + r;
+        }
+    }
+    const int TPR = N >= NPT ? N / NPT : 1;
+    const int RG = 256 / TPR;
+    const int my_rg = tid / TPR, my_c = tid % TPR;
+    const int64_t tiles_per_group = (g.M + R - 1) / R;
+    const int64_t n_tiles = g.n_groups * tiles_per_group;
+    const bool single = g.n_groups == 1 && g.kv == 1;
+    auto load_B = [&](int64_t u) {
+        const int64_t ub = g.uR ? g.uR[u] : 0;
+        const T* B = arena + g.b_off + ub * g.b_key;
+        for (int e = tid; e < K * N; e += 256) {
+            const int k = e / N, n = e % N;
+            Bs[k * ldB + n] = B[scatter(k, g.bpk, g.nbk) + scatter(n, g.bpn, g.nbn)];
+        }
+    };
+    auto issue = [&](int64_t tile, T* buf) {
+        const int64_t grp = tile / tiles_per_group;
+        const int64_t mt = tile % tiles_per_group;
+        const int64_t u0 = g.gstart ? g.gstart[grp] : 0;
+        const int64_t ua = g.uL ? g.uL[u0] : 0;
+        const T* A = arena + g.a_off + ua * g.a_key + scatter(mt * R, g.apm, g.nam);
+        const int64_t rows_left = g.M - mt * R;
+#pragma unroll
+        for (int j = 0; j < kStreamEPT; ++j) {
+            if (slot[j] < 0) continue;
+            if (rows_left >= R || (slot[j] % ldA) < rows_left) cp_async_el(buf + slot[j], A + off[j]);
+            else buf[slot[j]] = czero<T>();
+        }
+    };
+    if (single) load_B(0);
+    int64_t tile = blockIdx.x;
+    if (tile < n_tiles) issue(tile, buf0);
+    cp_async_commit();
+    for (int it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
+        T* cur = (it & 1) ? buf1 : buf0;
+        T* nxt = (it & 1) ? buf0 : buf1;
+        if (tile + gridDim.x < n_tiles) issue(tile + gridDim.x, nxt);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int64_t grp = tile / tiles_per_group;
+        const int64_t mt = tile % tiles_per_group;
+        const int64_t u0 = g.gstart ? g.gstart[grp] : 0;
+        const int64_t u1 = g.gstart ? g.gstart[grp + 1] : g.kv;
+        const int64_t rows_left = g.M - mt * R;
+        for (int64_t u = u0; u < u1; ++u) {
+            if (!single) {
+                load_B(u);
+                __syncthreads();
+            }
+            if (my_c * NPT < N) {
+                for (int r = my_rg; r < R && r < rows_left; r += RG) {
+                    T acc[NPT];
+#pragma unroll
+                    for (int j = 0; j < NPT; ++j) acc[j] = czero<T>();
+                    for (int k = 0; k < K; ++k) {
+                        const T a = cur[k * ldA + r];
+                        T b[NPT];
+                        load_vec<NPT>(Bs + k * ldB + my_c * NPT, b);
+#pragma unroll
+                        for (int j = 0; j < NPT; ++j) acc[j] = cfma(acc[j], a, b[j]);
+                    }
+                    store_vec<NPT>(arena + g.c_off + u * g.c_key + (mt * R + r) * N + my_c * NPT, acc);
+                }
+            }
+            if (!single) __syncthreads();
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+template <typename T>
+cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena, cudaStream_t st) {
+    const size_t a_sz = (size_t(g.K) * (s.R + 1) + 1) & ~size_t(1);
+    const size_t smem = sizeof(T) * (2 * a_sz + size_t(g.K) * (g.N + 2));
+    const int64_t tiles = g.n_groups * ((g.M + s.R - 1) / s.R);
+    const int grid = grid_for(tiles, 1, 152 * 8);
+    switch (s.npt) {
+#define XEB_STREAM_CASE(P)                                                                                   \
+    case P: {                                                                                                \
+        static bool set = false;                                                                             \
+        if (!set) {                                                                                          \
+            cudaFuncSetAttribute(k_gemm_stream<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); \
+            set = true;                                                                                      \
+        }                                                                                                    \
+        k_gemm_stream<T, P><<<grid, 256, smem, st>>>(g, s, arena);                                           \
+        break;                                                                                               \
+    }
+        XEB_STREAM_CASE(1)
+        XEB_STREAM_CASE(2)
+        XEB_STREAM_CASE(4)
+        XEB_STREAM_CASE(8)
+        XEB_STREAM_CASE(16)
+#undef XEB_STREAM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // ---- a6/a7 -------------------------------------------------------------------------
 
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
@@ -543,6 +729,8 @@ template cudaError_t launch_permute<float2>(const PermDesc&, const float2*, floa
 template cudaError_t launch_permute<double2>(const PermDesc&, const double2*, double2*, cudaStream_t);
 template cudaError_t launch_gemm<float2>(int, const GemmDesc&, float2*, cudaStream_t);
 template cudaError_t launch_gemm<double2>(int, const GemmDesc&, double2*, cudaStream_t);
+template cudaError_t launch_gemm_stream<float2>(const GemmDesc&, const StreamDesc&, float2*, cudaStream_t);
+template cudaError_t launch_gemm_stream<double2>(const GemmDesc&, const StreamDesc&, double2*, cudaStream_t);
 template cudaError_t launch_root_accum<float2>(const float2*, double2*, int64_t, cudaStream_t);
 template cudaError_t launch_root_accum<double2>(const double2*, double2*, int64_t, cudaStream_t);
 

@@ -67,7 +67,37 @@ struct GemmDesc {
     int64_t n_groups;
 };
 
-enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3 };
+// Streaming tile of the memory-bound contraction kernel: R rows x all K of A
+// occupy tile index bits 0..T-1 in ascending address order; tile bit i sits
+// at address bit pos[i] and is a bit of k if (is_k >> i) & 1, else of r.
+struct StreamDesc {
+    int R, tm, T, npt;
+    uint32_t is_k;
+    int8_t pos[32];
+};
+
+enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4 };
+constexpr int kStreamMaxK = 64, kStreamMaxN = 64;
+constexpr int kStreamEPT = 8;   // A-tile elements per thread
+
+// tcgen05 split-precision contraction (one key, M % 128 == 0, 16 <= K, N <= 64).
+// Tile bits of one K-chunk: the 7 lowest row bits and the 4 lowest summed
+// bits, in ascending address order (pos / is_k as in StreamDesc); the
+// remaining summed bits select the chunk (chunk_off).
+struct TcDesc {
+    int64_t M;
+    int K2, N2, n_chunks, tmem_cols;
+    int64_t a_off, b_off, c_off;
+    int nam, nbk, nbn, T;
+    uint32_t is_k;
+    int8_t apm[kMaxLegs], bpk[kMaxLegs], bpn[kMaxLegs];
+    int8_t pos[16];
+    int32_t chunk_off[4];
+    float* wimg;          // scratch: split, swizzled image of the real-expanded B
+    int32_t* err;         // error word (timeouts)
+};
+constexpr int32_t kErrTimeout = 0x40000000;  // | role code
+size_t tc_wimg_floats(const TcDesc& t);
 
 // ---- launch wrappers (all asynchronous on `st`) --------------------------------
 cudaError_t launch_trie_keys(const TrieDesc* d_desc, int n_nodes, const uint64_t* bits, int k,
@@ -82,7 +112,10 @@ cudaError_t launch_permute(const PermDesc& p, const T* src, T* dst, cudaStream_t
 template <typename T>
 cudaError_t launch_gemm(int kernel, const GemmDesc& g, T* arena, cudaStream_t st);
 template <typename T>
+cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena, cudaStream_t st);
+template <typename T>
 cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStream_t st);
+cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);
 cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k,
                               double2* amps, double* partials, int n_blocks, double* result,
                               int n_qubits, cudaStream_t st);

@@ -464,6 +464,26 @@ Costs tree_costs(const Analysis& an, const Program& prog, uint64_t k) {
     return c;
 }
 
+double estimate_time(const Analysis& an, const Program& prog, int precision, size_t elem) {
+    const double bw = 6.6e12 * 0.6;                        // bytes/s reached by streaming kernels
+    const double simt = precision == XEB_PREC_FP64 ? 0.3e12 : 10.0e12 * 0.5;  // complex MAC/s
+    const double tc = 1.0e15 / 3.0 / 8.0 * 0.6;            // 3 TF32 products per complex MAC
+    double t = 0;
+    for (const Op& op : prog.ops) {
+        if (op.kind == OP_PERM) {
+            t += 2.0 * double(op.keys) * std::ldexp(1.0, op.r) * double(elem) / bw + 3e-6;
+            continue;
+        }
+        const double cmac = double(op.kv) * double(op.M) * double(op.N) * double(op.K);
+        const double bytes = double(elem) * (double(an.nodes[op.a_node].kv) * std::ldexp(1.0, op.a_rank) +
+                                             double(an.nodes[op.b_node].kv) * std::ldexp(1.0, op.b_rank) +
+                                             double(op.kv) * double(op.M) * double(op.N));
+        const double rate = (precision == XEB_PREC_TF32X3 && tc_eligible(op)) ? tc : simt;
+        t += std::max(cmac / rate, bytes / bw) + 3e-6;
+    }
+    return t;
+}
+
 // ---- planners ---------------------------------------------------------------------
 
 Tree greedy_tree(const Network& net, DistinctCounter& dc, const std::vector<int>& sliced,

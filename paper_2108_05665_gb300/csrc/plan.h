@@ -111,6 +111,20 @@ struct Costs {
 };
 Costs tree_costs(const Analysis& an, const Program& prog, uint64_t k);
 
+// Contractions the tcgen05 split-precision kernel takes: one key, 128-row
+// tiles, 16 <= K, N <= 64 complex.
+inline bool tc_eligible(const Op& op) {
+    return op.kind == OP_GEMM && op.kv == 1 && op.M >= 128 && op.M % 128 == 0 && op.K >= 16 && op.K <= 64 &&
+           op.N >= 16 && op.N <= 64;
+}
+
+// Estimated device time of one slice (seconds) from a simple efficiency
+// profile of GB300: per contraction max(flop time, HBM time) + launch cost.
+// The objective uses log2 of it in place of log2(C + alpha RW) (App. A, last
+// paragraph of "Slicing": a measured efficiency profile replaces the flop and
+// read/write counts).
+double estimate_time(const Analysis& an, const Program& prog, int precision, size_t elem);
+
 // ---- planners ----------------------------------------------------------------
 Tree greedy_tree(const Network& net, DistinctCounter& dc, const std::vector<int>& sliced,
                  uint64_t seed, double noise);

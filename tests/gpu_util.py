@@ -20,8 +20,11 @@ def run(circ, bits, tree=None, slices=None, precision=B.XEB_PREC_FP32, planner=N
     k = len(bits)
     bits_dev = torch.from_numpy(np.asarray(bits, dtype=np.uint64).view(np.int64).copy()).cuda()
     out = torch.empty(2 * k, dtype=torch.float64, device="cuda")
+    B.xeb_plan_profile(plan.handle, True)
     B.xeb_set_bitstrings(plan.handle, bits_dev.data_ptr(), k, st)
     B.xeb_amplitudes(plan.handle, out.data_ptr(), st)
     F, m1, m2 = B.xeb_fidelity(plan.handle, st)
+    plan.profile = B.xeb_plan_profile_read(plan.handle)
+    B.xeb_plan_profile(plan.handle, False)
     amps = out.cpu().numpy().view(np.complex128).copy()
     return amps, F, plan

@@ -23,12 +23,16 @@ def fixture():
     return w.circuit(), np.asarray(z["bitstrings"], dtype=np.uint64), z["amplitudes"], float(z["F"])
 
 
-@pytest.mark.parametrize("precision", [B.XEB_PREC_FP32])
+@pytest.mark.parametrize("precision", [B.XEB_PREC_FP32, B.XEB_PREC_TF32X3])
 def test_grid5x6_all_amplitudes(fixture, precision):
     circ, bits, ref, F_ref = fixture
     amps, F, plan = run(circ, bits, precision=precision)
+    if precision == B.XEB_PREC_TF32X3:
+        assert "gemm_tc" in plan.profile, plan.profile
     err = rel_err(amps, ref, circ.n_qubits)
     print("max rel err %.3e  median %.3e  |dF| %.3e" % (err.max(), np.median(err), abs(F - F_ref)))
     assert err.max() < 1e-5
-    assert abs(F - F_ref) < 1e-6
+    # 3xTF32: FP32 accumulation in the tensor cores truncates, biasing F by
+    # ~2 x the per-amplitude bias (measured 1.6e-5 here); FP32 meets 1e-6.
+    assert abs(F - F_ref) < (1e-6 if precision == B.XEB_PREC_FP32 else 2e-5)
     plan.close()
