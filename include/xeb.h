@@ -228,6 +228,23 @@ xeb_status xeb_plan_profile(struct xeb_plan_s* plan, int enable);
 xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* launches, double* flops,
                                  double* bytes);
 
+/* Linear XEB of k complex128 amplitudes already in device memory (amps_dev,
+ * 2*k doubles): writes F, the mean of 2^n p and the mean of (2^n p)^2 to
+ * out_dev (3 doubles, device) on `stream`, asynchronously, and allocates
+ * nothing.  The paper has no counterpart.  It exists for callers that cannot
+ * allocate device memory: a process whose device memory belongs to its own
+ * pool allocator (cudaMalloc there fails or competes with the pool), or a
+ * latency-critical caller that cannot take the implicit device
+ * synchronisation of an allocation.  Its block partial sums live in a fixed
+ * array inside the library (64 KiB on every device that loads the library,
+ * held until the process exits), which limits k to 16,777,216; larger k
+ * returns XEB_EINVAL.  The first call on a device looks up that array's
+ * device address (with the device current); make that first call before any
+ * stream capture.  All calls share the array, so calls whose kernels overlap
+ * on the GPU race. */
+xeb_status xeb_linear_xeb_noalloc(const double* amps_dev, size_t k, int n_qubits, double* out_dev,
+                                  uintptr_t stream);
+
 /* Thread-local message of the last failure in this thread. */
 const char* xeb_last_error(void);
 

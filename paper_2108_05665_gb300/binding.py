@@ -94,6 +94,8 @@ _PROTOS = {
     "xeb_plan_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_void_p]),
     "xeb_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "xeb_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp, _dblp, _dblp]),
+    "xeb_linear_xeb_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
     "xeb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -248,6 +250,11 @@ def xeb_plan_keys(plan, node: int, k: int, kv: int, stream: int):
     _check(load().xeb_plan_keys(plan, node, _ptr(key, ctypes.c_int32), _ptr(uL, ctypes.c_int32),
                                 _ptr(uR, ctypes.c_int32), ctypes.c_void_p(stream or None)))
     return key, uL[:kv], uR[:kv]
+
+
+def xeb_linear_xeb_noalloc(amps_dev_ptr: int, k: int, n_qubits: int, out_dev_ptr: int, stream: int):
+    _check(load().xeb_linear_xeb_noalloc(ctypes.c_void_p(amps_dev_ptr), k, n_qubits,
+                                         ctypes.c_void_p(out_dev_ptr), ctypes.c_void_p(stream or None)))
 
 
 KERNEL_CLASSES = ["trie", "leaves", "permute", "gemm_tiled", "gemm_gemv", "gemm_tail", "gemm_generic",

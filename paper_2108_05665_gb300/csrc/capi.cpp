@@ -22,6 +22,11 @@ xeb_status fail(xeb_status s, const std::string& msg) {
     g_err = msg;
     return s;
 }
+}  // namespace
+
+void xebp::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
 
 #define XEB_CUDA(call)                                                                       \
     do {                                                                                     \

@@ -15,6 +15,9 @@ namespace xebp {
 
 using cd = std::complex<double>;
 
+// Thread-local message returned by xeb_last_error().
+void set_last_error(const std::string& msg);
+
 // One leaf of the fused circuit network (convention of include/xeb.h).
 // Tensor axes: out_q (listed order) then legs; row-major, first axis slowest.
 struct Leaf {
