@@ -348,11 +348,12 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
             else for (int b = 2; b <= 10; ++b) bs.push_back(b);
             if (o.group_leaves > 0) gs = {o.group_leaves};
             else gs = {1, 2, 3, 4};
-            for (int b : bs)
-                for (int g : gs) {
-                    Tree t;
-                    if (sweep_tree(p->net, b, g, t)) cands.push_back({XEB_PLANNER_SWEEP, t});
-                }
+            for (int variant = 0; variant < 2; ++variant)
+                for (int b : bs)
+                    for (int g : gs) {
+                        Tree t;
+                        if (sweep_tree(p->net, b, g, t, variant)) cands.push_back({XEB_PLANNER_SWEEP, t});
+                    }
         }
         for (auto& c : cands) {
             Candidate cd_;

@@ -569,7 +569,78 @@ Tree greedy_tree(const Network& net, DistinctCounter& dc, const std::vector<int>
     return tree;
 }
 
-bool sweep_tree(const Network& net, int bmax, int G, Tree& tree) {
+// Frontier blocks over the body leaves (time order = leaf order).
+static std::vector<std::vector<int>> frontier_blocks(const Network& net, const std::vector<int>& body, int bmax) {
+    const int n = net.n;
+    std::vector<std::vector<int>> per_q(n);  // body leaves on each qubit, time order
+    for (int j : body)
+        for (int q : net.leaves[j].qubits) per_q[q].push_back(j);
+    std::vector<size_t> head(n, 0);
+    std::vector<char> done(net.leaves.size(), 0);
+    auto ready = [&](int j) {
+        for (int q : net.leaves[j].qubits)
+            if (head[q] >= per_q[q].size() || per_q[q][head[q]] != j) return false;
+        return true;
+    };
+    auto absorb = [&](int j, std::vector<int>& blk) {
+        done[j] = 1;
+        blk.push_back(j);
+        for (int q : net.leaves[j].qubits) ++head[q];
+    };
+    std::vector<std::vector<int>> blocks;
+    size_t left = body.size();
+    while (left > 0) {
+        int first = -1;
+        for (int j : body)
+            if (!done[j] && ready(j)) { first = j; break; }
+        if (first < 0) break;  // cannot happen for a circuit network
+        std::set<int> Q(net.leaves[first].qubits.begin(), net.leaves[first].qubits.end());
+        std::vector<int> blk;
+        for (;;) {
+            bool grew = false;
+            for (int q : Q) {
+                while (head[q] < per_q[q].size()) {
+                    const int j = per_q[q][head[q]];
+                    bool inside = ready(j);
+                    for (int qq : net.leaves[j].qubits)
+                        if (!Q.count(qq)) inside = false;
+                    if (!inside) break;
+                    absorb(j, blk);
+                    grew = true;
+                }
+            }
+            if (grew) continue;
+            // widen the window by the earliest ready gate that still fits
+            int best = -1;
+            for (int q : Q) {
+                if (head[q] >= per_q[q].size()) continue;
+                const int j = per_q[q][head[q]];
+                if (!ready(j)) continue;
+                std::set<int> U = Q;
+                U.insert(net.leaves[j].qubits.begin(), net.leaves[j].qubits.end());
+                if (int(U.size()) <= bmax && (best < 0 || j < best)) best = j;
+            }
+            if (best < 0) {
+                // no ready neighbour fits: take the earliest ready gate anywhere
+                // that fits (disjoint gates then share one pass over the state)
+                for (int j : body) {
+                    if (done[j] || !ready(j)) continue;
+                    std::set<int> U = Q;
+                    U.insert(net.leaves[j].qubits.begin(), net.leaves[j].qubits.end());
+                    if (int(U.size()) <= bmax) { best = j; break; }
+                }
+            }
+            if (best < 0) break;
+            Q.insert(net.leaves[best].qubits.begin(), net.leaves[best].qubits.end());
+        }
+        left -= blk.size();
+        std::sort(blk.begin(), blk.end());
+        blocks.push_back(blk);
+    }
+    return blocks;
+}
+
+bool sweep_tree(const Network& net, int bmax, int G, Tree& tree, int variant) {
     const int L = int(net.leaves.size());
     tree.clear();
     if (L < 2 || bmax < 2 || G < 1) return false;
@@ -622,6 +693,7 @@ bool sweep_tree(const Network& net, int bmax, int G, Tree& tree) {
     }
     std::sort(open.begin(), open.end(), [](const Blk& x, const Blk& y) { return x.created < y.created; });
     for (auto& b : open) closed.push_back(b.leaves);
+    if (variant == 1) closed = frontier_blocks(net, body, bmax);
     auto chain = [&](const std::vector<int>& lv) {
         int ref = -1 - lv[0];
         for (size_t t = 1; t < lv.size(); ++t) {

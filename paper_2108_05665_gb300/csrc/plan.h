@@ -131,6 +131,10 @@ double estimate_time(const Analysis& an, const Program& prog, int precision, siz
 // ---- planners ----------------------------------------------------------------
 Tree greedy_tree(const Network& net, DistinctCounter& dc, const std::vector<int>& sliced,
                  uint64_t seed, double noise);
-bool sweep_tree(const Network& net, int block_qubits, int group_leaves, Tree& out);
+// variant 0: blocks grow while consecutive gates fit in block_qubits qubits;
+// variant 1: frontier blocks -- a window of <= block_qubits qubits absorbs
+// every gate whose predecessors are done, then widens by the earliest ready
+// gate that still fits.
+bool sweep_tree(const Network& net, int block_qubits, int group_leaves, Tree& out, int variant = 0);
 
 }  // namespace xebp

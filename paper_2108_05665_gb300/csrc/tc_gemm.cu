@@ -15,11 +15,13 @@
 // accumulators that the epilogue adds in FP32 round-to-nearest.
 //
 // Roles (one CTA per SM, persistent over 128-row tiles):
-//   warps 0-3  gather A rows through the per-leg address positions, split
+//   warps 0-7  gather A rows through the per-leg address positions, split
 //              them and store big/small into a shared-memory stage in the
-//              128-byte-swizzled K-major layout the MMA reads;
-//   warp  8    allocates tensor memory and (one lane) issues the MMAs;
-//   warps 4-7  move finished accumulators from tensor memory to global C.
+//              128-byte-swizzled K-major layout the MMA reads; each thread
+//              keeps the loads of the next two chunks in flight while it
+//              converts the current one;
+//   warp  12   allocates tensor memory and (one lane) issues the MMAs;
+//   warps 8-11 move finished accumulators from tensor memory to global C.
 // W (big and small) stays in shared memory for the whole kernel.  Every wait
 // is bounded: after ~2 s a role records an error code, stops, and the CTA
 // drains outstanding MMAs and frees its tensor memory before returning.
@@ -31,9 +33,14 @@ namespace {
 
 constexpr int kTcRows = 128;       // rows per tile (UMMA M)
 constexpr int kChunkFloats = 32;   // one 128-byte swizzle atom along K
-constexpr int kStages = 3;
-constexpr int kLoaderThreads = 128;
-constexpr int kThreads = 288;      // 9 warps
+constexpr int kStages = 2;
+constexpr int kCStride = 33;       // staging row stride (floats): conflict-free both ways
+constexpr int kLoaderWarps = 8;
+constexpr int kLoaderThreads = 32 * kLoaderWarps;   // 256
+                                                     // warps 8-11: epilogue
+constexpr int kMmaWarp = kLoaderWarps + 4;           // warp 12: TMEM + MMA issue
+constexpr int kThreads = 32 * (kLoaderWarps + 5);    // 416
+constexpr int kElems = kTcRows * 16 / kLoaderThreads;  // A elements per loader thread per chunk (8)
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -172,7 +179,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     float* Wsmall = reinterpret_cast<float*>(sm + w_bytes);
     unsigned char* stage_base = sm + 2 * w_bytes;          // per stage: A big 16 KB, A small 16 KB
     const int stage_bytes = 2 * kTcRows * 128;
-    TcSmem* S = reinterpret_cast<TcSmem*>(stage_base + kStages * stage_bytes);
+    float* Cstage = reinterpret_cast<float*>(stage_base + kStages * stage_bytes);  // 4 warps x 32 x 33
+    TcSmem* S = reinterpret_cast<TcSmem*>(Cstage + 4 * 32 * kCStride);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = t.M / kTcRows;
 
@@ -189,12 +197,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&S->tfull[b], 1);
-            mbar_init(&S->tempty[b], 128);
+            mbar_init(&S->tempty[b], 128);  // the 4 epilogue warps
         }
         mbar_init(&S->drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)),
                      "r"(uint32_t(t.tmem_cols))
                      : "memory");
@@ -206,14 +214,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     tc_fence_after();
     const uint32_t tmem = S->tmem_base;
 
-    if (warp < 4) {
+    if (warp < kLoaderWarps) {
         // ---------------- A producer: gather, split, swizzle ----------------
-        // per-thread tile elements: e = tid + 128 j, tile bits (7 row bits +
+        // per-thread tile elements: e = tid + 256 j, tile bits (7 row bits +
         // 4 k bits of the chunk) in ascending address order
-        int32_t off[16];
-        uint32_t pos[16];
+        int32_t off[kElems];
+        uint32_t pos[kElems];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < kElems; ++j) {
             const int e = tid + kLoaderThreads * j;
             int r = 0, k = 0, ri = 0, ki = 0;
             int32_t o = 0;
@@ -226,37 +234,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
             off[j] = o;
             pos[j] = swz(uint32_t(r) * 128u + uint32_t(k) * 8u);
         }
-        uint32_t it = 0;
-        bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const int64_t total = my_tiles * t.n_chunks;
+        auto issue = [&](int64_t it, float2 (&v)[kElems]) {
+            if (it >= total) return;
+            const int64_t tile = blockIdx.x + (it / t.n_chunks) * int64_t(gridDim.x);
+            const int c = int(it % t.n_chunks);
+            const int64_t m0 = tile * kTcRows;
             int64_t row_base = 0;
-            {
-                const int64_t m0 = tile * kTcRows;
-                for (int i = 0; i < t.nam; ++i)
-                    if ((m0 >> i) & 1) row_base |= int64_t(1) << t.apm[i];
-            }
-            const float2* A = arena + t.a_off + row_base;
-            for (int c = 0; c < t.n_chunks; ++c, ++it) {
-                const int s = int(it % kStages);
-                const uint32_t use = it / kStages;
-                if (!mbar_wait(&S->empty[s], (use & 1) ^ 1, t.err, 1)) { ok = false; break; }
-                const float2* Ac = A + t.chunk_off[c];
-                float2 v[16];
+            for (int i = 7; i < t.nam; ++i)
+                if ((m0 >> i) & 1) row_base |= int64_t(1) << t.apm[i];
+            const float2* Ac = arena + t.a_off + row_base + t.chunk_off[c];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = Ac[off[j]];
-                unsigned char* sb = stage_base + s * stage_bytes;
+            for (int j = 0; j < kElems; ++j) v[j] = Ac[off[j]];
+        };
+        bool ok = true;
+        auto store = [&](int64_t it, const float2 (&v)[kElems]) {
+            if (!ok || it >= total) return;
+            const int s = int(it % kStages);
+            const uint32_t use = uint32_t(it / kStages);
+            if (!mbar_wait(&S->empty[s], (use & 1) ^ 1, t.err, 1)) { ok = false; return; }
+            unsigned char* sb = stage_base + s * stage_bytes;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float bx = tf32_rn(v[j].x), by = tf32_rn(v[j].y);
-                    *reinterpret_cast<float2*>(sb + pos[j]) = make_float2(bx, by);
-                    *reinterpret_cast<float2*>(sb + kTcRows * 128 + pos[j]) =
-                        make_float2(tf32_rn(v[j].x - bx), tf32_rn(v[j].y - by));
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&S->full[s]);
+            for (int j = 0; j < kElems; ++j) {
+                const float bx = tf32_rn(v[j].x), by = tf32_rn(v[j].y);
+                *reinterpret_cast<float2*>(sb + pos[j]) = make_float2(bx, by);
+                *reinterpret_cast<float2*>(sb + kTcRows * 128 + pos[j]) =
+                    make_float2(tf32_rn(v[j].x - bx), tf32_rn(v[j].y - by));
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&S->full[s]);
+        };
+        float2 va[kElems], vb[kElems], vc[kElems];
+        issue(0, va);
+        issue(1, vb);
+        for (int64_t it = 0; it < total && ok; it += 3) {
+            issue(it + 2, vc);
+            store(it, va);
+            issue(it + 3, va);
+            store(it + 1, vb);
+            issue(it + 4, vb);
+            store(it + 2, vc);
         }
-    } else if (warp == 8) {
+    } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(t.N2 >> 3) << 17) |
@@ -301,23 +321,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     } else {
         // ---------------- epilogue: tensor memory -> C ----------------
         const int q = warp & 3;                 // lane quarter of this warp
-        const int row = q * 32 + lane;
+        float* stg = Cstage + q * 32 * kCStride;
         uint32_t tcount = 0;
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tcount) {
             const uint32_t b = tcount & 1, ub = tcount >> 1;
             const bool got = mbar_wait(&S->tfull[b], ub & 1, t.err, 5);
             if (!__all_sync(0xffffffffu, got)) break;
             tc_fence_after();
-            float* C = reinterpret_cast<float*>(arena + t.c_off) + (tile * kTcRows + row) * int64_t(t.N2);
+            // rows q*32 .. q*32+31 of this tile; each 32-column slice goes
+            // through a padded staging buffer so that every warp store
+            // writes four full 128-byte row segments
+            float* Cw = reinterpret_cast<float*>(arena + t.c_off) + (tile * kTcRows + q * 32) * int64_t(t.N2);
             const uint32_t tb = tmem + (uint32_t(q * 32) << 16) + b * uint32_t(2 * t.N2);
             for (int c0 = 0; c0 < t.N2; c0 += 32) {
                 float v[32], w[32];
                 tmem_ld32(tb + uint32_t(c0), v);
                 tmem_ld32(tb + uint32_t(t.N2 + c0), w);
 #pragma unroll
-                for (int i = 0; i < 32; i += 4)
-                    *reinterpret_cast<float4*>(C + c0 + i) =
-                        make_float4(v[i] + w[i], v[i + 1] + w[i + 1], v[i + 2] + w[i + 2], v[i + 3] + w[i + 3]);
+                for (int i = 0; i < 32; ++i) stg[lane * kCStride + i] = v[i] + w[i];
+                __syncwarp();
+                const int rr = lane >> 3, cc = (lane & 7) * 4;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int row = rr + 4 * i;
+                    const float* src = stg + row * kCStride + cc;
+                    *reinterpret_cast<float4*>(Cw + int64_t(row) * t.N2 + c0 + cc) =
+                        make_float4(src[0], src[1], src[2], src[3]);
+                }
+                __syncwarp();
             }
             tc_fence_before();
             mbar_arrive(&S->tempty[b]);
@@ -325,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(t.tmem_cols))
                      : "memory");
@@ -336,7 +367,7 @@ size_t tc_wimg_floats(const TcDesc& t) { return size_t(2) * t.n_chunks * t.N2 * 
 
 size_t tc_smem_bytes(const TcDesc& t) {
     const size_t w_bytes = size_t(t.n_chunks) * t.N2 * 128;
-    return 1024 + 2 * w_bytes + size_t(kStages) * 2 * kTcRows * 128 + 256;
+    return 1024 + 2 * w_bytes + size_t(kStages) * 2 * kTcRows * 128 + 4 * 32 * kCStride * 4 + 256;
 }
 
 cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st) {
