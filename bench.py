@@ -46,6 +46,8 @@ def workload_desc(w):
 
 
 def load_bitstrings(w):
+    if w.name != WORKLOAD:  # profiling cases: uniform bitstrings
+        return inputs.uniform_bitstrings(w.n_qubits, w.k, w.bitstring_seed)
     z = np.load(FIXTURE)
     bits = np.asarray(z["bitstrings"], dtype=np.uint64)
     assert len(bits) == w.k
@@ -199,7 +201,8 @@ def main():
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
-    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid5x5_m12_k2000"],
+                    help="benchmark workload (default) or the small profiling case")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -209,7 +212,7 @@ def main():
     rank, world = dist_setup(args.gpus)
     build.build()
     B.load()
-    w = inputs.WORKLOADS[WORKLOAD]
+    w = inputs.WORKLOADS[args.workload]
     circ = w.circuit()
     bits = load_bitstrings(w)
     prec = {"fp32": B.XEB_PREC_FP32, "tf32x3": B.XEB_PREC_TF32X3}[args.precision]
@@ -279,20 +282,27 @@ def main():
     name, d = dom
     per_launch_ms = d["ms"] / d["launches"]
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    if name in ("gemm_tc",):
-        bound, unit = "tensor", "TFLOP/s"
+    # bound of the dominant kernel class: the larger of its flop time at the
+    # compute peak and its byte time at the HBM peak (algorithmic work)
+    hbm = pk["hbm_gbs"]
+    if name == "gemm_tc":
+        flop_peak = pk["bf16_tflops"] / 2.0 / 3.0   # TF32 = bf16/2; 3 TF32 products per useful flop
+        flop_note = "measured bf16 x nominal tf32/bf16 ratio 1/2, / 3 split products (" + pk_kind + ")"
+        flop_bound = "tensor"
+    else:
+        flop_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
+        flop_note = "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_max
+        flop_bound = "alu"
+    t_flop = d["flops"] / (flop_peak * 1e12)
+    t_byte = d["bytes"] / (hbm * 1e9)
+    if t_flop >= t_byte:
+        bound, unit = flop_bound, "TFLOP/s"
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-        peak = pk["bf16_tflops"] / 2.0  # tf32 = half of the bf16 dense rate
-        peak_note = "measured bf16 x nominal tf32/bf16 ratio 1/2 (" + pk_kind + ")"
-    elif name in ("gemm_tiled", "gemm_generic") and d["flops"] / max(d["bytes"], 1) > 12:
-        bound, unit = "alu", "TFLOP/s"
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
-        peak_note = "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_max
+        peak, peak_note = flop_peak, flop_note
     else:
         bound, unit = "hbm", "GB/s"
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        peak = pk["hbm_gbs"]
+        peak = hbm
         peak_note = "measured copy bandwidth (" + pk_kind + ")"
     eff_tflops = st["flops_per_slice"] * st["n_slices"] * args.steps * world / (ms_total / 1e3) / 1e12
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
@@ -301,7 +311,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32x3": "tf32x3"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "desc": workload_desc(w), "precision": args.precision,
+        "config": {"workload": w.name, "desc": workload_desc(w), "precision": args.precision,
                    "planner": ["given", "greedy", "sweep"][st["planner_used"]], "n_slices": st["n_slices"],
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
                    "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},
@@ -320,7 +330,7 @@ def main():
                     for kname, v in prof.items()},
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and w.name == WORKLOAD:
         t_full, g, G = cpu_oracle_sample(circ)
         line["cpu_baseline"] = {"value": k / t_full, "unit": "amplitudes/s", "cores": os.cpu_count(),
                                 "kind": "oracle",

@@ -210,6 +210,9 @@ WORKLOADS = {
     "grid5x6_m14_k10000": Workload("grid5x6_m14_k10000", 5, 6, 14, 10000, 1002,
                                    2002, ideal_fraction=0.5, ideal_seed=3002,
                                    trie_depth=10),
+    # 5x5 grid, 12 cycles, 2,000 uniform bitstrings: small profiling case
+    # (256 MB state, larger than L2).
+    "grid5x5_m12_k2000": Workload("grid5x5_m12_k2000", 5, 5, 12, 2000, 1004, 2004),
     # 5x8 grid, 12 cycles, 100,000 uniform bitstrings (sliced).
     "grid5x8_m12_k100000": Workload("grid5x8_m12_k100000", 5, 8, 12, 100000,
                                     1003, 2003),
