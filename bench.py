@@ -129,20 +129,7 @@ def dist_setup(n_gpus):
     return rank, world
 
 
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+from paper_2108_05665_gb300.dist import barrier, max_over_ranks  # noqa: E402
 
 
 def cpu_oracle_sample(circ, target_s=15.0):
