@@ -93,7 +93,7 @@ bool stream_tile(const Op& op, size_t elem, xebk::StreamDesc& s) {
     const int rg = 256 / tpr;
     int R = 1;
     while (2 * R <= op.M && 2 * R * op.K <= 256 * xebk::kStreamEPT && 2 * R <= rg * std::max(1, 16 / npt) &&
-           size_t(2 * R) * size_t(op.K) * elem <= 32 * 1024)
+           size_t(2 * R) * size_t(op.K) * elem <= 16 * 1024)
         R *= 2;
     if (R < 32 || R * op.K > 256 * xebk::kStreamEPT) return false;
     int tm = 0;

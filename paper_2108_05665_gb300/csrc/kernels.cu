@@ -513,9 +513,8 @@ __global__ void __launch_bounds__(256, 2) k_gemm_stream(const __grid_constant__ 
     const int R = s.R, K = int(g.K), N = int(g.N);
     const int ldA = R + 1, ldB = N + (NPT > 1 ? 2 : 1);
     const int a_sz = (K * ldA + 1) & ~1;
-    T* buf0 = reinterpret_cast<T*>(sm_stream);  // two A tiles [K][R+1], then B [K][ldB]
-    T* buf1 = buf0 + a_sz;
-    T* Bs = buf1 + a_sz;
+    T* bufs = reinterpret_cast<T*>(sm_stream);  // kStreamStages A tiles [K][R+1], then B [K][ldB]
+    T* Bs = bufs + kStreamStages * a_sz;
     const int tid = threadIdx.x;
     const int tile_elems = R * K;
     int32_t off[kStreamEPT];
@@ -567,21 +566,52 @@ __global__ void __launch_bounds__(256, 2) k_gemm_stream(const __grid_constant__ 
         }
     };
     if (single) load_B(0);
-    int64_t tile = blockIdx.x;
-    if (tile < n_tiles) issue(tile, buf0);
-    cp_async_commit();
-    for (int it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
-        T* cur = (it & 1) ? buf1 : buf0;
-        T* nxt = (it & 1) ? buf0 : buf1;
-        if (tile + gridDim.x < n_tiles) issue(tile + gridDim.x, nxt);
+    // ring of kStreamStages tiles: the loads of the next kStreamStages-1
+    // tiles are in flight while one tile is multiplied
+#pragma unroll
+    for (int p = 0; p < kStreamStages - 1; ++p) {
+        const int64_t tl = blockIdx.x + int64_t(p) * gridDim.x;
+        if (tl < n_tiles) issue(tl, bufs + p * a_sz);
         cp_async_commit();
-        cp_async_wait<1>();
+    }
+    int64_t tile = blockIdx.x;
+    for (int it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
+        T* cur = bufs + (it % kStreamStages) * a_sz;
+        const int64_t ahead = tile + int64_t(kStreamStages - 1) * gridDim.x;
+        if (ahead < n_tiles) issue(ahead, bufs + ((it + kStreamStages - 1) % kStreamStages) * a_sz);
+        cp_async_commit();
+        cp_async_wait<kStreamStages - 1>();
         __syncthreads();
         const int64_t grp = tile / tiles_per_group;
         const int64_t mt = tile % tiles_per_group;
         const int64_t u0 = g.gstart ? g.gstart[grp] : 0;
         const int64_t u1 = g.gstart ? g.gstart[grp + 1] : g.kv;
         const int64_t rows_left = g.M - mt * R;
+        if (N == 1 && !single) {
+            // memo-trie levels: many keys share this A tile; stage the B
+            // vectors of a batch of keys at once, then one (row, key) dot
+            // product per thread slot
+            const int kb_max = kStreamBKeys / K;
+            for (int64_t ub0 = u0; ub0 < u1; ub0 += kb_max) {
+                const int64_t left_keys = u1 - ub0;
+                const int nb = left_keys < kb_max ? int(left_keys) : kb_max;
+                for (int e = tid; e < nb * K; e += 256) {
+                    const int j = e / K, k = e % K;
+                    const int64_t ub = g.uR ? g.uR[ub0 + j] : 0;
+                    Bs[e] = arena[g.b_off + ub * g.b_key + scatter(k, g.bpk, g.nbk)];
+                }
+                __syncthreads();
+                const int rows = rows_left < R ? int(rows_left) : R;
+                for (int pr = tid; pr < rows * nb; pr += 256) {
+                    const int r = pr % rows, j = pr / rows;
+                    T acc = czero<T>();
+                    for (int k = 0; k < K; ++k) acc = cfma(acc, cur[k * ldA + r], Bs[j * K + k]);
+                    arena[g.c_off + (ub0 + j) * g.c_key + mt * R + r] = acc;
+                }
+                __syncthreads();
+            }
+            continue;
+        }
         for (int64_t u = u0; u < u1; ++u) {
             if (!single) {
                 load_B(u);
@@ -612,7 +642,8 @@ __global__ void __launch_bounds__(256, 2) k_gemm_stream(const __grid_constant__ 
 template <typename T>
 cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena, cudaStream_t st) {
     const size_t a_sz = (size_t(g.K) * (s.R + 1) + 1) & ~size_t(1);
-    const size_t smem = sizeof(T) * (2 * a_sz + size_t(g.K) * (g.N + 2));
+    const size_t b_sz = g.N == 1 ? size_t(kStreamBKeys) : size_t(g.K) * (g.N + 2);
+    const size_t smem = sizeof(T) * (kStreamStages * a_sz + b_sz);
     const int64_t tiles = g.n_groups * ((g.M + s.R - 1) / s.R);
     const int grid = grid_for(tiles, 1, 152 * 8);
     switch (s.npt) {

@@ -79,6 +79,8 @@ struct StreamDesc {
 enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4 };
 constexpr int kStreamMaxK = 64, kStreamMaxN = 64;
 constexpr int kStreamEPT = 8;   // A-tile elements per thread
+constexpr int kStreamStages = 4;  // A tiles in flight per CTA
+constexpr int kStreamBKeys = 2048;  // B elements staged per key batch (N == 1)
 
 // tcgen05 split-precision contraction (one key, M % 128 == 0, 16 <= K, N <= 64).
 // Tile bits of one K-chunk: the 7 lowest row bits and the 4 lowest summed
