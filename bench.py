@@ -187,8 +187,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tc-variant", default="tmem", choices=["tmem", "smem"],
+                    help="tensor-core kernel: B^T in tensor memory (default) or split B in shared memory")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid5x5_m12_k2000"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid5x5_m12_k2000", "grid3x9_m12_k2000"],
                     help="benchmark workload (default) or the small profiling case")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -205,6 +207,7 @@ def main():
     prec = {"fp32": B.XEB_PREC_FP32, "tf32x3": B.XEB_PREC_TF32X3}[args.precision]
     o = B.xeb_default_opts()
     o.precision = prec
+    o.reserved[1] = 1 if args.tc_variant == "smem" else 0
     try:
         plan = B.Plan(circ, bits, opts=o)
         plan.bind()
@@ -299,6 +302,7 @@ def main():
         "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32x3": "tf32x3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w.name, "desc": workload_desc(w), "precision": args.precision,
+                   "tc_variant": args.tc_variant,
                    "planner": ["given", "greedy", "sweep"][st["planner_used"]], "n_slices": st["n_slices"],
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
                    "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},

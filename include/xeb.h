@@ -111,7 +111,11 @@ typedef struct {
     uint64_t mem_budget;  /* M_max in bytes for the contraction arena            */
     uint64_t seed;        /* planner randomisation                               */
     int greedy_trials;    /* randomised greedy restarts                          */
-    int reserved[7];
+    int reserved[7];      /* [0] = 1: permute operands into [free][summed] blocks
+                             before each contraction instead of gathering them in
+                             place; [1] = 1: tensor-core kernel with the split B
+                             in shared memory instead of B^T in tensor memory;
+                             others 0 */
 } xeb_plan_opts;
 
 typedef struct {

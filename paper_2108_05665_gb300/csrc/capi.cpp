@@ -37,7 +37,8 @@ namespace {
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-constexpr int GK_TC = 100;  // tcgen05 split-precision kernel (tc_gemm.cu)
+constexpr int GK_TC = 100;   // tcgen05 split-precision kernel, split W in smem (tc_gemm.cu)
+constexpr int GK_TC2 = 101;  // tcgen05 split-precision kernel, W^T in tensor memory (tc_gemm2.cu)
 
 struct GemmLaunch {
     int kernel;
@@ -48,7 +49,7 @@ struct GemmLaunch {
 
 // Tensor-core eligibility and descriptor of a contraction (one key, 128-row
 // tiles, 16 <= K, N <= 64 complex, tile offsets within 32 bits).
-bool tc_tile(const Op& op, xebk::TcDesc& t) {
+bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits) {
     if (!tc_eligible(op)) return false;
     if (op.a_pos_m.size() > size_t(xebk::kMaxLegs)) return false;
     std::memset(&t, 0, sizeof(t));
@@ -58,7 +59,7 @@ bool tc_tile(const Op& op, xebk::TcDesc& t) {
     t.n_chunks = t.K2 / 32;
     t.tmem_cols = 4 * t.N2;  // 2 buffers x (big, small) accumulators
     std::vector<std::pair<int, int>> bits;
-    for (int i = 0; i < 7; ++i) bits.push_back({op.a_pos_m[i], 0});
+    for (int i = 0; i < row_bits; ++i) bits.push_back({op.a_pos_m[i], 0});
     for (int i = 0; i < 4; ++i) bits.push_back({op.a_pos_k[i], 1});
     std::sort(bits.begin(), bits.end());
     for (auto& b : bits)
@@ -675,8 +676,8 @@ void build_launches(xeb_plan_s* p) {
                 d.n_groups = 1;
             }
             if (op.M == 1 && op.N == 1) g.kernel = xebk::GK_TAIL;
-            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc)) {
-                g.kernel = GK_TC;
+            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc, p->opts.reserved[1] == 1 ? 7 : 6)) {
+                g.kernel = p->opts.reserved[1] == 1 ? GK_TC : GK_TC2;
                 g.tc.a_off = d.a_off;
                 g.tc.b_off = d.b_off;
                 g.tc.c_off = d.c_off;
@@ -739,11 +740,13 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             return false;
         }
         if ((ka > 1 || kb > 1) && !g.uL) { why = "gemm without key tables"; return false; }
-        if (p->gemms[i].kernel == GK_TC) {
+        if (p->gemms[i].kernel == GK_TC || p->gemms[i].kernel == GK_TC2) {
             const xebk::TcDesc& t = p->gemms[i].tc;
-            if (t.M != g.M || t.M % 128 != 0 || t.K2 != 2 * g.K || t.N2 != 2 * g.N || t.K2 % 32 != 0 ||
-                t.N2 % 32 != 0 || t.N2 > 128 || t.n_chunks * 32 != t.K2 || t.n_chunks > 4 || t.T != 11 ||
-                g.kv != 1 || xebk::tc_wimg_floats(t) * 4 > size_t(2 * 4 * 128 * 32 * 4)) {
+            const int row_bits = p->gemms[i].kernel == GK_TC ? 7 : 6;
+            if (t.M != g.M || t.M % (int64_t(1) << row_bits) != 0 || t.K2 != 2 * g.K || t.N2 != 2 * g.N ||
+                t.K2 % 32 != 0 || t.N2 % 32 != 0 || t.N2 > 128 || t.K2 > 128 || t.n_chunks * 32 != t.K2 ||
+                t.n_chunks > 4 || t.T != row_bits + 4 || g.kv != 1 ||
+                xebk::tc_wimg_floats(t) * 4 > size_t(2 * 4 * 128 * 32 * 4)) {
                 why = "tensor-core tile of node " + std::to_string(op.node);
                 return false;
             }
@@ -752,7 +755,7 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             for (int i = 0; i < t.T; ++i) hi |= int64_t(1) << t.pos[i];
             hi += t.chunk_off[t.n_chunks - 1];
             int64_t rowhi = 0;
-            for (int i = 7; i < t.nam; ++i) rowhi |= int64_t(1) << t.apm[i];
+            for (int i = row_bits; i < t.nam; ++i) rowhi |= int64_t(1) << t.apm[i];
             if (!inside(op.a_buf, t.a_off, t.a_off + rowhi + hi) || !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1)) {
                 why = "tensor-core operand of node " + std::to_string(op.node);
                 return false;
@@ -813,10 +816,13 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                                         double(op.kv) * double(op.M * op.N));
                 static const int cls_of[5] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
                                               XEB_KC_GEMM_TAIL, XEB_KC_GEMM_STREAM};
-                ProfScope ps(p, st, g.kernel == GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by);
+                ProfScope ps(p, st, g.kernel >= GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by);
                 if (g.kernel == GK_TC) {
                     if constexpr (sizeof(T) == 8)
                         XEB_CUDA(xebk::launch_tc_gemm(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st));
+                } else if (g.kernel == GK_TC2) {
+                    if constexpr (sizeof(T) == 8)
+                        XEB_CUDA(xebk::launch_tc_gemm2(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st));
                 } else if (g.kernel == xebk::GK_STREAM) {
                     XEB_CUDA(xebk::launch_gemm_stream<T>(g.d, g.s, arena, st));
                 } else {

@@ -118,6 +118,9 @@ cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena,
 template <typename T>
 cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);
+// Variant with W^T in tensor memory and a deep cp.async ring (64-row tiles,
+// tile bits = 6 row bits + 4 k bits).
+cudaError_t launch_tc_gemm2(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);
 cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k,
                               double2* amps, double* partials, int n_blocks, double* result,
                               int n_qubits, cudaStream_t st);

@@ -213,6 +213,9 @@ WORKLOADS = {
     # 5x5 grid, 12 cycles, 2,000 uniform bitstrings: small profiling case
     # (256 MB state, larger than L2).
     "grid5x5_m12_k2000": Workload("grid5x5_m12_k2000", 5, 5, 12, 2000, 1004, 2004),
+    # 3x9 grid, 12 cycles, 2,000 uniform bitstrings: profiling case whose body
+    # contractions have K = N = 64 like the benchmark's (1 GB state).
+    "grid3x9_m12_k2000": Workload("grid3x9_m12_k2000", 3, 9, 12, 2000, 1005, 2005),
     # 5x8 grid, 12 cycles, 100,000 uniform bitstrings (sliced).
     "grid5x8_m12_k100000": Workload("grid5x8_m12_k100000", 5, 8, 12, 100000,
                                     1003, 2003),

@@ -171,14 +171,18 @@ def grid4x5():
     return circ, bits, statevec.amplitudes(circ, bits)
 
 
-@pytest.mark.parametrize("planner,block", [(B.XEB_PLANNER_SWEEP, 6), (B.XEB_PLANNER_SWEEP, 5),
-                                           (B.XEB_PLANNER_SWEEP, 4), (B.XEB_PLANNER_AUTO, 0)])
-def test_tf32x3_tensor_core_parity(grid4x5, planner, block):
+@pytest.mark.parametrize("planner,block,smem_w", [(B.XEB_PLANNER_SWEEP, 6, 0), (B.XEB_PLANNER_SWEEP, 5, 0),
+                                                  (B.XEB_PLANNER_SWEEP, 4, 0), (B.XEB_PLANNER_AUTO, 0, 0),
+                                                  (B.XEB_PLANNER_SWEEP, 6, 1), (B.XEB_PLANNER_SWEEP, 4, 1)])
+def test_tf32x3_tensor_core_parity(grid4x5, planner, block, smem_w):
     """3xTF32 tcgen05 contractions against the FP64 oracle: the tensor-core
-    kernel must actually run (M = 2^13..2^16 rows, K, N = 16..64)."""
+    kernel must actually run (M = 2^13..2^16 rows, K, N = 16..64).  smem_w
+    selects the variant with the split W resident in shared memory instead of
+    W^T in tensor memory."""
     circ, bits, ref = grid4x5
     o = B.xeb_default_opts()
     o.block_qubits = block
+    o.reserved[1] = smem_w
     amps, F, plan = run(circ, bits, precision=B.XEB_PREC_TF32X3, planner=planner, opts=o)
     err = rel_err(amps, ref, 20)
     print("tf32x3 block %d: max rel err %.2e, tc launches %s" % (block, err.max(), plan.profile.get("gemm_tc")))
