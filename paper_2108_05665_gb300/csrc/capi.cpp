@@ -49,7 +49,7 @@ struct GemmLaunch {
 
 // Tensor-core eligibility and descriptor of a contraction (one key, 128-row
 // tiles, 16 <= K, N <= 64 complex, tile offsets within 32 bits).
-bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits) {
+bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits, bool tmem_variant) {
     if (!tc_eligible(op)) return false;
     if (op.a_pos_m.size() > size_t(xebk::kMaxLegs)) return false;
     std::memset(&t, 0, sizeof(t));
@@ -58,8 +58,26 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits) {
     t.N2 = int(2 * op.N);
     t.n_chunks = t.K2 / 32;
     t.tmem_cols = 4 * t.N2;  // 2 buffers x (big, small) accumulators
+    // rows of a tile: for the tensor-memory kernel the rows whose output bits
+    // are lowest (legs the parent sums) come first so every tile writes whole
+    // contiguous runs; then the lowest remaining rows
+    std::vector<int> tile_rows;
+    if (tmem_variant) {
+        const int n_low = int(op.c_hint.size());
+        for (size_t i = 0; i < op.a_pos_m.size(); ++i)
+            if (op.c_pos_m[i] < n_low) tile_rows.push_back(int(i));
+        for (size_t i = 0; i < op.a_pos_m.size() && int(tile_rows.size()) < row_bits; ++i)
+            if (std::find(tile_rows.begin(), tile_rows.end(), int(i)) == tile_rows.end()) tile_rows.push_back(int(i));
+        if (int(tile_rows.size()) != row_bits) return false;
+        std::sort(tile_rows.begin(), tile_rows.end());
+    } else {
+        for (int i = 0; i < row_bits; ++i) tile_rows.push_back(i);
+        // the shared-memory variant writes row-major results only
+        for (size_t i = 0; i < op.c_pos_m.size(); ++i)
+            if (op.c_pos_m[i] != int(op.c_pos_n.size() + i)) return false;
+    }
     std::vector<std::pair<int, int>> bits;
-    for (int i = 0; i < row_bits; ++i) bits.push_back({op.a_pos_m[i], 0});
+    for (int i : tile_rows) bits.push_back({op.a_pos_m[i], 0});
     for (int i = 0; i < 4; ++i) bits.push_back({op.a_pos_k[i], 1});
     std::sort(bits.begin(), bits.end());
     for (auto& b : bits)
@@ -78,6 +96,25 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits) {
     }
     t.nam = int(op.a_pos_m.size());
     for (int i = 0; i < t.nam; ++i) t.apm[i] = int8_t(op.a_pos_m[i]);
+    t.n_ext = 0;
+    for (int i = 0; i < t.nam; ++i) {
+        if (std::find(tile_rows.begin(), tile_rows.end(), i) != tile_rows.end()) continue;
+        t.ext_apos[t.n_ext] = int8_t(op.a_pos_m[i]);
+        t.ext_cpos[t.n_ext] = int8_t(op.c_pos_m[i]);
+        ++t.n_ext;
+    }
+    std::vector<std::array<int, 3>> st;  // (C bit, is column, bit index)
+    for (size_t r = 0; r < tile_rows.size(); ++r) st.push_back({op.c_pos_m[tile_rows[r]], 0, int(r)});
+    for (size_t j = 0; j < op.c_pos_n.size(); ++j) st.push_back({op.c_pos_n[j], 1, int(j)});
+    std::sort(st.begin(), st.end());
+    if (st.size() > 16) return false;
+    t.Tst = int(st.size());
+    t.st_is_n = 0;
+    for (int i = 0; i < t.Tst; ++i) {
+        t.st_pos[i] = int8_t(st[i][0]);
+        t.st_idx[i] = int8_t(st[i][2]);
+        if (st[i][1]) t.st_is_n |= 1u << i;
+    }
     t.nbk = int(op.b_pos_k.size());
     t.nbn = int(op.b_pos_n.size());
     for (int i = 0; i < t.nbk; ++i) t.bpk[i] = int8_t(op.b_pos_k[i]);
@@ -277,7 +314,8 @@ bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& slic
     cand.tree = tree;
     if (!analyze(net, tree, sliced, cand.an, err)) return false;
     fill_counts(cand.an, dc);
-    build_program(cand.an, cand.prog, o.reserved[0] == 0);
+    build_program(cand.an, cand.prog, o.reserved[0] == 0,
+                  o.precision == XEB_PREC_TF32X3 && o.reserved[1] != 1);
     plan_memory(cand.prog);
     cand.costs = tree_costs(cand.an, cand.prog, k);
     cand.arena_bytes = cand.prog.arena_elems * int64_t(elem);
@@ -664,6 +702,15 @@ void build_launches(xeb_plan_s* p) {
             for (int t = 0; t < d.nak; ++t) d.apk[t] = int8_t(op.a_pos_k[t]);
             for (int t = 0; t < d.nbk; ++t) d.bpk[t] = int8_t(op.b_pos_k[t]);
             for (int t = 0; t < d.nbn; ++t) d.bpn[t] = int8_t(op.b_pos_n[t]);
+            d.c_natural = 1;
+            for (int t = 0; t < d.nam; ++t) {
+                d.cpm[t] = int8_t(op.c_pos_m[t]);
+                if (op.c_pos_m[t] != d.nbn + t) d.c_natural = 0;
+            }
+            for (int t = 0; t < d.nbn; ++t) {
+                d.cpn[t] = int8_t(op.c_pos_n[t]);
+                if (op.c_pos_n[t] != t) d.c_natural = 0;
+            }
             const int ti = p->trie_of_node[op.node];
             if (ti >= 0) {
                 const xebk::TrieDesc& t = p->trie[ti];
@@ -676,7 +723,7 @@ void build_launches(xeb_plan_s* p) {
                 d.n_groups = 1;
             }
             if (op.M == 1 && op.N == 1) g.kernel = xebk::GK_TAIL;
-            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc, p->opts.reserved[1] == 1 ? 7 : 6)) {
+            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc, 7, p->opts.reserved[1] != 1)) {
                 g.kernel = p->opts.reserved[1] == 1 ? GK_TC : GK_TC2;
                 g.tc.a_off = d.a_off;
                 g.tc.b_off = d.b_off;
@@ -740,9 +787,22 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             return false;
         }
         if ((ka > 1 || kb > 1) && !g.uL) { why = "gemm without key tables"; return false; }
+        {
+            const int rc = g.nam + g.nbn;
+            std::vector<int> seen(rc, 0);
+            for (int t2 = 0; t2 < g.nam; ++t2)
+                if (g.cpm[t2] < 0 || g.cpm[t2] >= rc || seen[g.cpm[t2]]++) { why = "result positions"; return false; }
+            for (int t2 = 0; t2 < g.nbn; ++t2)
+                if (g.cpn[t2] < 0 || g.cpn[t2] >= rc || seen[g.cpn[t2]]++) { why = "result positions"; return false; }
+            if (!g.c_natural && p->gemms[i].kernel != GK_TC2) {
+                why = "non row-major result for a kernel that writes row-major only (node " +
+                      std::to_string(op.node) + ")";
+                return false;
+            }
+        }
         if (p->gemms[i].kernel == GK_TC || p->gemms[i].kernel == GK_TC2) {
             const xebk::TcDesc& t = p->gemms[i].tc;
-            const int row_bits = p->gemms[i].kernel == GK_TC ? 7 : 6;
+            const int row_bits = 7;
             if (t.M != g.M || t.M % (int64_t(1) << row_bits) != 0 || t.K2 != 2 * g.K || t.N2 != 2 * g.N ||
                 t.K2 % 32 != 0 || t.N2 % 32 != 0 || t.N2 > 128 || t.K2 > 128 || t.n_chunks * 32 != t.K2 ||
                 t.n_chunks > 4 || t.T != row_bits + 4 || g.kv != 1 ||
@@ -756,12 +816,33 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             hi += t.chunk_off[t.n_chunks - 1];
             int64_t rowhi = 0;
             for (int i = row_bits; i < t.nam; ++i) rowhi |= int64_t(1) << t.apm[i];
-            if (!inside(op.a_buf, t.a_off, t.a_off + rowhi + hi) || !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1)) {
+            if ((p->gemms[i].kernel == GK_TC && !inside(op.a_buf, t.a_off, t.a_off + rowhi + hi)) ||
+                !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1)) {
                 why = "tensor-core operand of node " + std::to_string(op.node);
                 return false;
             }
             for (int i = 0; i < t.T; ++i)
                 if (t.pos[i] < 0 || t.pos[i] >= op.a_rank) { why = "tensor-core tile positions"; return false; }
+            if (p->gemms[i].kernel == GK_TC2) {
+                const int rc = g.nam + g.nbn;
+                if (t.n_ext + row_bits != g.nam || t.Tst != row_bits + g.nbn || (1 << (t.Tst > 5 ? t.Tst - 5 : 0)) > 256) {
+                    why = "tensor-core result tile of node " + std::to_string(op.node);
+                    return false;
+                }
+                std::vector<int> seen(rc, 0);
+                for (int i2 = 0; i2 < t.n_ext; ++i2)
+                    if (t.ext_cpos[i2] < 0 || t.ext_cpos[i2] >= rc || seen[t.ext_cpos[i2]]++) { why = "tc ext"; return false; }
+                for (int i2 = 0; i2 < t.Tst; ++i2)
+                    if (t.st_pos[i2] < 0 || t.st_pos[i2] >= rc || seen[t.st_pos[i2]]++) { why = "tc store"; return false; }
+                int64_t ahi = 0;
+                for (int i2 = 0; i2 < t.n_ext; ++i2) ahi |= int64_t(1) << t.ext_apos[i2];
+                int64_t thi = 0;
+                for (int i2 = 0; i2 < t.T; ++i2) thi |= int64_t(1) << t.pos[i2];
+                if (!inside(op.a_buf, t.a_off, t.a_off + ahi + thi + t.chunk_off[t.n_chunks - 1])) {
+                    why = "tensor-core operand rows of node " + std::to_string(op.node);
+                    return false;
+                }
+            }
         }
         if (p->gemms[i].kernel == xebk::GK_STREAM) {
             const xebk::StreamDesc& sd = p->gemms[i].s;

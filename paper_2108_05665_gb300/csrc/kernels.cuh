@@ -61,6 +61,8 @@ struct GemmDesc {
     int64_t a_off, a_key, b_off, b_key, c_off, c_key;
     int nam, nak, nbk, nbn;
     int8_t apm[kMaxLegs], apk[kMaxLegs], bpk[kMaxLegs], bpn[kMaxLegs];
+    int8_t cpm[kMaxLegs], cpn[kMaxLegs];  // result address bit of m bit i / n bit i
+    int c_natural;                        // 1: result is row-major [M][N]
     const int32_t* uL;      // nullptr -> 0
     const int32_t* uR;      // nullptr -> 0
     const int32_t* gstart;  // groups of keys by uL (nullptr -> one group)
@@ -95,6 +97,14 @@ struct TcDesc {
     int8_t apm[kMaxLegs], bpk[kMaxLegs], bpn[kMaxLegs];
     int8_t pos[16];
     int32_t chunk_off[4];
+    // (tensor-memory variant) rows outside the tile: A and C address bits;
+    // the result tile's bits in ascending C address: C bit, is-column flag
+    // and the row / column bit index
+    int n_ext;
+    int8_t ext_apos[kMaxLegs], ext_cpos[kMaxLegs];
+    int Tst;
+    uint32_t st_is_n;
+    int8_t st_pos[16], st_idx[16];
     float* wimg;          // scratch: split, swizzled image of the real-expanded B
     int32_t* err;         // error word (timeouts)
 };

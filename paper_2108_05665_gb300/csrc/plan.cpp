@@ -297,7 +297,7 @@ std::vector<int> concat(const std::vector<int>& a, const std::vector<int>& b) {
 }
 }  // namespace
 
-void build_program(const Analysis& an, Program& prog, bool gather) {
+void build_program(const Analysis& an, Program& prog, bool gather, bool consumer_layout) {
     const int N = int(an.nodes.size());
     const int L = an.L;
     int n_legs = 0;
@@ -322,6 +322,17 @@ void build_program(const Analysis& an, Program& prog, bool gather) {
     }
     std::vector<char> inS(std::max(n_legs, 1), 0);
     std::vector<int> s1, f1, s2, f2;
+    // legs each node's parent sums (the node's share of its parent's K)
+    std::vector<std::vector<int>> summed_by_parent(N);
+    for (int v = L; v < N; ++v) {
+        const Node& nd = an.nodes[v];
+        std::vector<int> S;
+        for (int l : an.nodes[nd.l].legs)
+            if (std::find(an.nodes[nd.r].legs.begin(), an.nodes[nd.r].legs.end(), l) != an.nodes[nd.r].legs.end())
+                S.push_back(l);
+        summed_by_parent[nd.l] = S;
+        summed_by_parent[nd.r] = S;
+    }
     // address bit of `leg` in layout `lay` (slowest first)
     auto pos_of = [](const std::vector<int>& lay, int leg) {
         const int i = int(std::find(lay.begin(), lay.end(), leg) - lay.begin());
@@ -414,7 +425,20 @@ void build_program(const Analysis& an, Program& prog, bool gather) {
         for (size_t t = fa.size(); t-- > 0;) lay.push_back(fa[t]);
         std::vector<int> lc;
         for (size_t t = fb.size(); t-- > 0;) lc.push_back(fb[t]);
-        prog.layout[v] = concat(lay, lc);
+        std::vector<int> out = concat(lay, lc);
+        if (gather && consumer_layout && v != N - 1 && elems_of(v) >= (int64_t(1) << 20) &&
+            !summed_by_parent[v].empty() && summed_by_parent[v].size() <= 6 && tc_eligible(op)) {
+            // stable partition: the legs the parent sums move to the lowest bits
+            const std::vector<int>& sp = summed_by_parent[v];
+            auto in_sp = [&](int leg) { return std::find(sp.begin(), sp.end(), leg) != sp.end(); };
+            std::vector<int> hi, lo;
+            for (int leg : out) (in_sp(leg) ? lo : hi).push_back(leg);
+            out = concat(hi, lo);
+            op.c_hint = sp;
+        }
+        prog.layout[v] = out;
+        for (int leg : fa) op.c_pos_m.push_back(pos_of(out, leg));
+        for (int leg : fb) op.c_pos_n.push_back(pos_of(out, leg));
         prog.ops.push_back(op);
         for (int l : S) inS[l] = 0;
     }

@@ -86,6 +86,10 @@ struct Op {
     // address bit pos[i] of the operand tensor (legs have dimension 2)
     std::vector<int> a_pos_m, a_pos_k, b_pos_k, b_pos_n;
     int a_rank = 0, b_rank = 0;
+    // output addressing: bit i of m / n sits at address bit c_pos_m[i] /
+    // c_pos_n[i] of the result (row-major [M][N] when natural)
+    std::vector<int> c_pos_m, c_pos_n;
+    std::vector<int> c_hint;  // legs of this result that its parent sums (low bits)
 };
 
 struct Buffer {
@@ -106,7 +110,10 @@ struct Program {
 // gather = true: contractions read their operands in place through per-leg
 // address positions (no permutation passes); false: permute operands into
 // [free][summed] blocks first.
-void build_program(const Analysis& an, Program& prog, bool gather);
+// consumer_layout = true: a result of >= 2^20 elements is laid out with the
+// legs its parent sums as the lowest address bits, so the parent reads whole
+// contiguous rows.
+void build_program(const Analysis& an, Program& prog, bool gather, bool consumer_layout = false);
 void plan_memory(Program& prog);  // emulation-mode allocator: exact arena peak
 
 struct Costs {

@@ -367,7 +367,7 @@ size_t tc_wimg_floats(const TcDesc& t) { return size_t(2) * t.n_chunks * t.N2 * 
 
 size_t tc_smem_bytes(const TcDesc& t) {
     const size_t w_bytes = size_t(t.n_chunks) * t.N2 * 128;
-    return 1024 + 2 * w_bytes + size_t(kStages) * 2 * kTcRows * 128 + 4 * 32 * kCStride * 4 + 256;
+    return 1024 + 2 * w_bytes + size_t(kStages) * 2 * kTcRows * 128 + 4 * 32 * kCStride * 4 + sizeof(TcSmem);
 }
 
 cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st) {

@@ -18,8 +18,9 @@
 // read D^T from tensor memory (lane = output column), transpose it through a
 // padded shared buffer and write whole rows of C.
 //
-// Tensor memory: columns [0, 128) W^T big, [128, 256) W^T small, then two
-// accumulator buffers of 128 columns (64 big + 64 small).  Every wait is
+// Tensor memory: columns [0, 128) W^T big, [128, 256) W^T small, [256, 384)
+// big*big accumulator, [384, 512) cross-term accumulator (128-row tiles: one
+// MMA instruction covers 128 state rows).  Every wait is
 // bounded (2 s, error word); the CTA always drains its MMAs and frees tensor
 // memory before returning.
 #include "kernels.cuh"
@@ -28,17 +29,19 @@ namespace xebk {
 
 namespace {
 
-constexpr int kRows = 64;            // state rows per tile (UMMA N)
+constexpr int kRows = 128;           // state rows per tile (UMMA N)
 constexpr int kM = 128;              // W^T rows (UMMA M), N2 padded to 128
 constexpr int kChunk = 32;           // floats of K' per chunk (one swizzle atom)
-constexpr int kRing = 8;             // chunk stages
+constexpr int kRing = 4;             // chunk stages (16 KB big + 16 KB small each)
 constexpr int kProdWarps = 4;
 constexpr int kProd = 32 * kProdWarps;            // 128 producer threads
 constexpr int kEpiWarp0 = kProdWarps;             // warps 4-7
 constexpr int kMmaWarp = kProdWarps + 4;          // warp 8
 constexpr int kThreads = 32 * (kProdWarps + 5);   // 288
-constexpr int kPerThread = kRows * 16 / kProd;    // 8 complex elements per producer per chunk
-constexpr int kStageBytes = 2 * kRows * 128;      // big + small, 8 KB each
+constexpr int kPerThread = kRows * 16 / kProd;    // 16 complex elements per producer per chunk
+constexpr int kRowBits = 7;
+constexpr int kTab = 256;                         // result-tile table entries
+constexpr int kStageBytes = 2 * kRows * 128;      // big + small, 16 KB each
 constexpr int kCStride = 132;                     // floats per staged output row
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -142,6 +145,8 @@ __device__ __forceinline__ void tm_st32(uint32_t ta, const float* v) {
 }
 struct Sm2 {
     uint64_t full[kRing], empty[kRing], tfull[2], tempty[2], wready, drain, epi;
+    int64_t hi_glob[kTab];
+    int32_t hi_slot[kTab];
     uint32_t tmem;
 };
 
@@ -214,10 +219,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
                 if (!bar_wait(&S->empty[s], (use & 1) ^ 1, t.err, 11)) { ok = false; break; }
                 if (tile_of != tcur) {
                     tile_of = tcur;
-                    const int64_t m0 = tcur * kRows;
                     base = 0;
-                    for (int i = 6; i < t.nam; ++i)
-                        if ((m0 >> i) & 1) base |= int64_t(1) << t.apm[i];
+                    for (int i = 0; i < t.n_ext; ++i)
+                        if ((tcur >> i) & 1) base |= int64_t(1) << t.ext_apos[i];
                 }
                 const float2* A = arena + t.a_off + base + t.chunk_off[c];
                 unsigned char* sb = ring + s * kStageBytes;
@@ -255,10 +259,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
             fence_after();
             uint32_t it = 0, tc = 0;
             for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++tc) {
-                const uint32_t b = tc & 1, ub = tc >> 1;
+                const uint32_t b = 0, ub = tc;  // one accumulator pair (TMEM is full)
                 if (!bar_wait(&S->tempty[b], (ub & 1) ^ 1, t.err, 13)) break;
                 fence_after();
-                const uint32_t d_big = tmem + 256 + b * 128, d_small = d_big + 64;
+                const uint32_t d_big = tmem + 256, d_small = d_big + kRows;
                 for (int ch = 0; ch < nch; ++ch, ++it) {
                     const int s = int(it % kRing);
                     const uint32_t use = it / kRing;
@@ -321,6 +325,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
         uint32_t tc = 0, ep = 0;
         const uint32_t lanes = uint32_t(q * 32) << 16;
         const int etid = tid - 32 * kEpiWarp0;   // 0..127
+        // result tile element e (bits in ascending C address) -> staging slot
+        // and C offset; split as e = e_hi * 32 + lane: the lane part once per
+        // thread, the e_hi part in a per-CTA table
+        int lo_slot = 0;
+        int64_t lo_glob = 0;
+        {
+            int r = 0, n = 0;
+            for (int i = 0; i < 5 && i < t.Tst; ++i) {
+                const int bit = (lane >> i) & 1;
+                if (!bit) continue;
+                if ((t.st_is_n >> i) & 1) n |= 1 << t.st_idx[i];
+                else r |= 1 << t.st_idx[i];
+                lo_glob |= int64_t(1) << t.st_pos[i];
+            }
+            lo_slot = r * (kCStride / 2) + n;
+        }
+        const int n_hi = t.Tst > 5 ? 1 << (t.Tst - 5) : 1;
+        for (int h = etid; h < n_hi; h += 128) {  // n_hi <= kTab
+            int r = 0, n = 0;
+            int64_t g = 0;
+            for (int i = 5; i < t.Tst; ++i) {
+                if (!((h >> (i - 5)) & 1)) continue;
+                if ((t.st_is_n >> i) & 1) n |= 1 << t.st_idx[i];
+                else r |= 1 << t.st_idx[i];
+                g |= int64_t(1) << t.st_pos[i];
+            }
+            S->hi_slot[h] = r * (kCStride / 2) + n;
+            S->hi_glob[h] = g;
+        }
         // bounded sync of the four epilogue warps (an aborting warp cannot
         // leave the others blocked)
         auto epi_sync = [&]() {
@@ -329,30 +362,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
             ++ep;
             return ok;
         };
-        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tc) {
-            const uint32_t b = tc & 1, ub = tc >> 1;
+        bool table_ok = __all_sync(0xffffffffu, epi_sync());  // table visible to all four warps
+        for (int64_t tile = blockIdx.x; tile < n_tiles && table_ok; tile += gridDim.x, ++tc) {
+            const uint32_t b = 0, ub = tc;
             const bool got = bar_wait(&S->tfull[b], ub & 1, t.err, 16);
             if (!__all_sync(0xffffffffu, got)) break;
             fence_after();
             // D^T: lane = output column np, column = tile row
-            const uint32_t db = tmem + 256 + b * 128;
+            const uint32_t db = tmem + 256;
             for (int r0 = 0; r0 < kRows; r0 += 32) {
                 float v[32], w[32];
                 tm_ld32(db + lanes + uint32_t(r0), v);
-                tm_ld32(db + lanes + 64 + uint32_t(r0), w);
+                tm_ld32(db + lanes + kRows + uint32_t(r0), w);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) cst[(r0 + i) * kCStride + np] = v[i] + w[i];
             }
             fence_before();
             bar_arrive(&S->tempty[b]);
             if (!__all_sync(0xffffffffu, epi_sync())) break;
-            // whole rows of C: one warp writes one row (N2 floats) per step
-            float* C = reinterpret_cast<float*>(arena + t.c_off) + tile * kRows * int64_t(t.N2);
-            for (int e = etid * 4; e < kRows * t.N2; e += 128 * 4) {
-                const int row = e / t.N2, col = e % t.N2;
-                const float* src = cst + row * kCStride + col;
-                *reinterpret_cast<float4*>(C + int64_t(row) * t.N2 + col) = make_float4(src[0], src[1], src[2], src[3]);
-            }
+            // the tile's results in ascending C address order (contiguous runs)
+            int64_t cbase = 0;
+            for (int i = 0; i < t.n_ext; ++i)
+                if ((tile >> i) & 1) cbase |= int64_t(1) << t.ext_cpos[i];
+            float2* C = arena + t.c_off + cbase + lo_glob;
+            const float2* st2 = reinterpret_cast<const float2*>(cst);
+            for (int h = q; h < n_hi; h += 4) C[S->hi_glob[h]] = st2[S->hi_slot[h] + lo_slot];
             if (!__all_sync(0xffffffffu, epi_sync())) break;
         }
     }
@@ -364,7 +398,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
     }
 }
 
-size_t tc2_smem_bytes() { return 1024 + size_t(kRing) * kStageBytes + size_t(kRows) * kCStride * 4 + 256; }
+// 1024 bytes of alignment slack + ring + output staging + barriers/tables
+size_t tc2_smem_bytes() {
+    return 1024 + size_t(kRing) * kStageBytes + size_t(kRows) * kCStride * 4 + sizeof(Sm2);
+}
+static_assert(sizeof(Sm2) % 8 == 0 && 1024 + kRing * kStageBytes + kRows * kCStride * 4 + sizeof(Sm2) <= 232448,
+              "tensor-memory contraction exceeds the shared memory of one CTA");
 
 cudaError_t launch_tc_gemm2(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st) {
     static bool attr = false;
