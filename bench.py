@@ -187,6 +187,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the step kernel by kernel instead of replaying one captured CUDA graph")
     ap.add_argument("--tc-variant", default="tmem", choices=["tmem", "smem"],
                     help="tensor-core kernel: B^T in tensor memory (default) or split B in shared memory")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
@@ -208,6 +210,7 @@ def main():
     o = B.xeb_default_opts()
     o.precision = prec
     o.reserved[1] = 1 if args.tc_variant == "smem" else 0
+    o.reserved[2] = 1 if args.eager else 0
     try:
         plan = B.Plan(circ, bits, opts=o)
         plan.bind()
@@ -303,6 +306,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": w.name, "desc": workload_desc(w), "precision": args.precision,
                    "tc_variant": args.tc_variant,
+                   "launch": "kernel by kernel" if args.eager else "one CUDA graph per step",
                    "planner": ["given", "greedy", "sweep"][st["planner_used"]], "n_slices": st["n_slices"],
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
                    "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},

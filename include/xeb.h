@@ -115,6 +115,8 @@ typedef struct {
                              before each contraction instead of gathering them in
                              place; [1] = 1: tensor-core kernel with the split B
                              in shared memory instead of B^T in tensor memory;
+                             [2] = 1: launch kernels one by one instead of
+                             replaying one captured CUDA graph per step;
                              others 0 */
 } xeb_plan_opts;
 
@@ -176,15 +178,20 @@ size_t xeb_plan_device_bytes(struct xeb_plan_s* plan);
 xeb_status xeb_plan_bind(struct xeb_plan_s* plan, void* workspace, size_t bytes,
                          uintptr_t stream);
 
-/* Memo key tables (a1, on the device): read `k` bitstrings from device memory
- * (must equal the plan's k and give the plan's counts; a mismatch returns
- * XEB_EDEVICE) and build, for every node, the key id of each bitstring and
- * the children's key ids (uL, uR) of each key. */
+/* Copy `k` bitstrings from device memory into the plan (k must equal the
+ * plan's k, and the bitstrings must give the plan's counts -- a mismatch is
+ * reported as XEB_EDEVICE by xeb_fidelity).  The memo key tables (a1: the key
+ * id of each bitstring per node, the children's key ids (uL, uR) of each key)
+ * are rebuilt on the device by the next xeb_amplitudes / xeb_plan_keys. */
 xeb_status xeb_set_bitstrings(struct xeb_plan_s* plan, const uint64_t* bitstrings_dev,
                               size_t k, uintptr_t stream);
 
-/* Contract every slice (a2..a6) and write the k amplitudes, in input order,
- * as complex128 to device memory out_dev [2*k doubles]. */
+/* One step: build the key tables of the current bitstrings (a1), contract
+ * every slice (a2..a6) and write the k amplitudes, in input order, as
+ * complex128 to device memory out_dev [2*k doubles] (NULL: the plan's own
+ * buffer), plus the XEB sums (a7).  The first call per output pointer
+ * captures the step as a CUDA graph on a private stream; later calls replay
+ * it on `stream` (not while profiling, or with opts.reserved[2] = 1). */
 xeb_status xeb_amplitudes(struct xeb_plan_s* plan, double* out_dev, uintptr_t stream);
 
 /* Linear XEB of the last xeb_amplitudes call (Eq. 1): F, mean of 2^n p and

@@ -204,6 +204,21 @@ struct xeb_plan_s {
         double flops, bytes;
     };
     std::vector<Rec> pending;
+    // A whole step (key tables + every slice + XEB) as one CUDA graph,
+    // captured on a private stream and launched on the caller's stream.  A
+    // profiled graph also holds an event-record node before and after every
+    // kernel; its events are read before the graph is launched again, so two
+    // profiled graphs alternate and the host never waits on the step in flight.
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        void* out = nullptr;
+        std::vector<Rec> recs;
+        bool launched = false;
+    };
+    cudaStream_t cap_stream = nullptr;
+    StepGraph graph_plain, graph_prof[2];
+    int graph_prof_next = 0;
+    bool capturing_prof = false;
     std::vector<cudaEvent_t> event_pool;
     double prof_ms[XEB_N_KC] = {0}, prof_n[XEB_N_KC] = {0}, prof_flops[XEB_N_KC] = {0}, prof_bytes[XEB_N_KC] = {0};
 };
@@ -231,19 +246,26 @@ struct ProfScope {
         : p(p_), st(st_), cls(cls_), flops(flops_), bytes(bytes_) {
         if (p->profiling) {
             a = take_event(p);
-            cudaEventRecord(a, st);
+            record(a);
         }
+    }
+    void record(cudaEvent_t e) {
+        // inside a capture an external record becomes an event-record node
+        if (p->capturing_prof)
+            cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else
+            cudaEventRecord(e, st);
     }
     ~ProfScope() {
         if (!p->profiling || !a) return;
         cudaEvent_t b = take_event(p);
-        cudaEventRecord(b, st);
+        record(b);
         p->pending.push_back({cls, a, b, flops, bytes});
     }
 };
 
-void drain_profile(xeb_plan_s* p) {
-    for (auto& r : p->pending) {
+void accumulate(xeb_plan_s* p, const std::vector<xeb_plan_s::Rec>& recs) {
+    for (const auto& r : recs) {
         float ms = 0.f;
         if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
             p->prof_ms[r.cls] += ms;
@@ -251,10 +273,31 @@ void drain_profile(xeb_plan_s* p) {
             p->prof_flops[r.cls] += r.flops;
             p->prof_bytes[r.cls] += r.bytes;
         }
+    }
+}
+
+void drain_profile(xeb_plan_s* p) {
+    accumulate(p, p->pending);
+    for (auto& r : p->pending) {
         p->event_pool.push_back(r.a);
         p->event_pool.push_back(r.b);
     }
     p->pending.clear();
+    for (auto& g : p->graph_prof)
+        if (g.launched) {
+            accumulate(p, g.recs);
+            g.launched = false;
+        }
+}
+
+void drop_graph(xeb_plan_s* p, xeb_plan_s::StepGraph& g) {
+    if (g.launched) accumulate(p, g.recs);
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& r : g.recs) {
+        p->event_pool.push_back(r.a);
+        p->event_pool.push_back(r.b);
+    }
+    g = xeb_plan_s::StepGraph();
 }
 }  // namespace
 
@@ -448,6 +491,9 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
 
 extern "C" void xeb_plan_destroy(xeb_plan_s* p) {
     if (!p) return;
+    drop_graph(p, p->graph_plain);
+    for (auto& g : p->graph_prof) drop_graph(p, g);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     drain_profile(p);
     for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
     if (p->owns && p->ws) cudaFree(p->ws);
@@ -983,6 +1029,7 @@ extern "C" xeb_status xeb_plan_bind(xeb_plan_s* p, void* workspace, size_t bytes
         p->owns = true;
     }
     p->ws_bytes = p->bytes_total;
+    XEB_CUDA(xebk::prepare_kernels());
     build_launches(p);
     {
         std::string why;
@@ -1019,21 +1066,91 @@ extern "C" xeb_status xeb_set_bitstrings(xeb_plan_s* p, const uint64_t* bits_dev
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* tables = p->ws + p->off_tables;
     XEB_CUDA(cudaMemcpyAsync(tables + p->t_bits, bits_dev, k * 8, cudaMemcpyDeviceToDevice, st));
-    return build_tables(p, st);
+    p->tables_ready = false;  // rebuilt by the next step (a1 runs inside it)
+    return XEB_OK;
 }
+
+namespace {
+// One whole step: memo key tables (a1) then every slice (a2-a6) and the XEB
+// fold (a7).
+xeb_status enqueue_step(xeb_plan_s* p, double2* out, cudaStream_t st) {
+    xeb_status s = build_tables(p, st);
+    if (s != XEB_OK) return s;
+    return p->elem == 8 ? run_slices<float2>(p, out, st) : run_slices<double2>(p, out, st);
+}
+}  // namespace
+
+namespace {
+// Capture one step into g (its profiled form when p->profiling is on).
+xeb_status capture_step(xeb_plan_s* p, xeb_plan_s::StepGraph& g, double2* out) {
+    drop_graph(p, g);
+    if (!p->cap_stream) XEB_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    if (p->profiling) {  // two events per launch, created before the capture opens
+        const size_t launches = 2 + (size_t(1) << p->sliced.size()) * (p->prog.ops.size() + 2);
+        while (p->event_pool.size() < 2 * launches) {
+            cudaEvent_t e = nullptr;
+            XEB_CUDA(cudaEventCreate(&e));
+            p->event_pool.push_back(e);
+        }
+    }
+    XEB_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    std::vector<xeb_plan_s::Rec> outside;
+    outside.swap(p->pending);
+    p->capturing_prof = p->profiling;
+    xeb_status s = enqueue_step(p, out, p->cap_stream);
+    p->capturing_prof = false;
+    g.recs.swap(p->pending);
+    p->pending.swap(outside);
+    cudaGraph_t cg = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->cap_stream, &cg);
+    if (s == XEB_OK && ec != cudaSuccess)
+        s = fail(XEB_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec));
+    if (s == XEB_OK) {
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, cg, 0);
+        if (ei != cudaSuccess) {
+            g.exec = nullptr;
+            s = fail(XEB_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+        }
+    }
+    if (cg) cudaGraphDestroy(cg);
+    if (s != XEB_OK) {
+        drop_graph(p, g);
+        return s;
+    }
+    g.out = out;
+    return XEB_OK;
+}
+}  // namespace
 
 extern "C" xeb_status xeb_amplitudes(xeb_plan_s* p, double* out_dev, uintptr_t stream) {
     xeb_status s = check_bound(p);
     if (s != XEB_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!p->tables_ready) {
-        s = build_tables(p, st);
-        if (s != XEB_OK) return s;
-    }
     double2* out = out_dev ? reinterpret_cast<double2*>(out_dev)
                            : reinterpret_cast<double2*>(p->ws + p->off_tables + p->t_amps);
-    s = p->elem == 8 ? run_slices<float2>(p, out, st) : run_slices<double2>(p, out, st);
-    if (s == XEB_OK) p->amps_ready = true;
+    const bool use_graph = p->opts.reserved[2] == 0 && p->sliced.size() <= 6;
+    if (!use_graph) {
+        s = enqueue_step(p, out, st);
+    } else {
+        xeb_plan_s::StepGraph* g = &p->graph_plain;
+        if (p->profiling) {
+            g = &p->graph_prof[p->graph_prof_next];
+            p->graph_prof_next ^= 1;
+            if (g->launched) {  // read the events of its previous launch first
+                accumulate(p, g->recs);
+                g->launched = false;
+            }
+        }
+        if (!g->exec || g->out != out) s = capture_step(p, *g, out);
+        if (s == XEB_OK) {
+            XEB_CUDA(cudaGraphLaunch(g->exec, st));
+            g->launched = p->profiling;
+        }
+    }
+    if (s == XEB_OK) {
+        p->amps_ready = true;
+        p->tables_ready = true;
+    }
     return s;
 }
 
@@ -1067,8 +1184,6 @@ extern "C" xeb_status xeb_run(xeb_plan_s* p, const uint64_t* bits_host, size_t k
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* tables = p->ws + p->off_tables;
     XEB_CUDA(cudaMemcpyAsync(tables + p->t_bits, bits_host, k * 8, cudaMemcpyHostToDevice, st));
-    s = build_tables(p, st);
-    if (s != XEB_OK) return s;
     double* amps_dev = reinterpret_cast<double*>(tables + p->t_amps);
     s = xeb_amplitudes(p, amps_dev, stream);
     if (s != XEB_OK) return s;
@@ -1084,6 +1199,10 @@ extern "C" xeb_status xeb_plan_keys(xeb_plan_s* p, int node, int32_t* key, int32
     const int ti = p->trie_of_node[v];
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* tables = p->ws + p->off_tables;
+    if (!p->tables_ready) {
+        s = build_tables(p, st);
+        if (s != XEB_OK) return s;
+    }
     if (ti < 0) {  // no output bits: a single key
         if (key) std::fill(key, key + p->k, 0);
         if (uL) uL[0] = 0;

@@ -179,13 +179,6 @@ cudaError_t launch_trie_keys(const TrieDesc* d_desc, int n_nodes, const uint64_t
     int kpad = 2;
     while (kpad < k) kpad <<= 1;
     const size_t smem = size_t(kpad) * (sizeof(uint64_t) + sizeof(int32_t));
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_trie_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(size_t(kMaxTrieK) * 12));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
     k_trie_keys<<<n_nodes, 1024, smem, st>>>(d_desc, bits, k, kpad, pi, tables, err);
     return cudaGetLastError();
 }
@@ -647,16 +640,10 @@ cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena,
     const int64_t tiles = g.n_groups * ((g.M + s.R - 1) / s.R);
     const int grid = grid_for(tiles, 1, 152 * 8);
     switch (s.npt) {
-#define XEB_STREAM_CASE(P)                                                                                   \
-    case P: {                                                                                                \
-        static bool set = false;                                                                             \
-        if (!set) {                                                                                          \
-            cudaFuncSetAttribute(k_gemm_stream<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); \
-            set = true;                                                                                      \
-        }                                                                                                    \
-        k_gemm_stream<T, P><<<grid, 256, smem, st>>>(g, s, arena);                                           \
-        break;                                                                                               \
-    }
+#define XEB_STREAM_CASE(P)                                    \
+    case P:                                                   \
+        k_gemm_stream<T, P><<<grid, 256, smem, st>>>(g, s, arena); \
+        break;
         XEB_STREAM_CASE(1)
         XEB_STREAM_CASE(2)
         XEB_STREAM_CASE(4)
@@ -751,6 +738,28 @@ cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64
     if (e != cudaSuccess) return e;
     k_xeb_final<<<1, 256, 0, st>>>(partials, n_blocks, k, n_qubits, result);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_tc_kernels();
+
+cudaError_t prepare_kernels() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_trie_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(size_t(kMaxTrieK) * 12));
+    if (e != cudaSuccess) return e;
+#define XEB_PREP_STREAM(T, P)                                                                            \
+    e = cudaFuncSetAttribute(k_gemm_stream<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024); \
+    if (e != cudaSuccess) return e;
+    XEB_PREP_STREAM(float2, 1) XEB_PREP_STREAM(float2, 2) XEB_PREP_STREAM(float2, 4)
+    XEB_PREP_STREAM(float2, 8) XEB_PREP_STREAM(float2, 16)
+    XEB_PREP_STREAM(double2, 1) XEB_PREP_STREAM(double2, 2) XEB_PREP_STREAM(double2, 4)
+    XEB_PREP_STREAM(double2, 8) XEB_PREP_STREAM(double2, 16)
+#undef XEB_PREP_STREAM
+    e = prepare_tc_kernels();
+    if (e != cudaSuccess) return e;
+    done = true;
+    return cudaSuccess;
 }
 
 // ---- instantiations ------------------------------------------------------------------

@@ -112,6 +112,9 @@ constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 size_t tc_wimg_floats(const TcDesc& t);
 
 // ---- launch wrappers (all asynchronous on `st`) --------------------------------
+// Raise the dynamic shared-memory limits of every kernel (once per process,
+// before any stream capture).
+cudaError_t prepare_kernels();
 cudaError_t launch_trie_keys(const TrieDesc* d_desc, int n_nodes, const uint64_t* bits, int k,
                              const int32_t* pi, char* tables, int32_t* err, cudaStream_t st);
 cudaError_t launch_trie_links(const TrieDesc* d_desc, const int* d_internal, int n_internal,

@@ -370,13 +370,11 @@ size_t tc_smem_bytes(const TcDesc& t) {
     return 1024 + 2 * w_bytes + size_t(kStages) * 2 * kTcRows * 128 + 4 * 32 * kCStride * 4 + sizeof(TcSmem);
 }
 
+cudaError_t prepare_tc1() {
+    return cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+}
+
 cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     k_tc_prep<<<64, 256, 0, st>>>(t, arena);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -405,13 +405,15 @@ size_t tc2_smem_bytes() {
 static_assert(sizeof(Sm2) % 8 == 0 && 1024 + kRing * kStageBytes + kRows * kCStride * 4 + sizeof(Sm2) <= 232448,
               "tensor-memory contraction exceeds the shared memory of one CTA");
 
+cudaError_t prepare_tc1();
+
+cudaError_t prepare_tc_kernels() {
+    cudaError_t e = prepare_tc1();
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tc_gemm2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem_bytes()));
+}
+
 cudaError_t launch_tc_gemm2(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem_bytes()));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     const int64_t tiles = t.M / kRows;
     const int grid = int(tiles < n_sms ? tiles : n_sms);
     k_tc_gemm2<<<grid, kThreads, tc2_smem_bytes(), st>>>(t, arena);
