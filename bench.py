@@ -191,6 +191,8 @@ def main():
                     help="launch the step kernel by kernel instead of replaying one captured CUDA graph")
     ap.add_argument("--tc-variant", default="tmem", choices=["tmem", "smem"],
                     help="tensor-core kernel: B^T in tensor memory (default) or split B in shared memory")
+    ap.add_argument("--tc-loads", default="tma", choices=["tma", "gather"],
+                    help="tensor-core A operand: TMA boxes where A is row-major (default) or plain-load gathers")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid5x5_m12_k2000", "grid3x9_m12_k2000"],
                     help="benchmark workload (default) or the small profiling case")
@@ -211,6 +213,7 @@ def main():
     o.precision = prec
     o.reserved[1] = 1 if args.tc_variant == "smem" else 0
     o.reserved[2] = 1 if args.eager else 0
+    o.reserved[3] = 1 if args.tc_loads == "gather" else 0
     try:
         plan = B.Plan(circ, bits, opts=o)
         plan.bind()
@@ -305,7 +308,7 @@ def main():
         "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32x3": "tf32x3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w.name, "desc": workload_desc(w), "precision": args.precision,
-                   "tc_variant": args.tc_variant,
+                   "tc_variant": args.tc_variant, "tc_loads": args.tc_loads,
                    "launch": "kernel by kernel" if args.eager else "one CUDA graph per step",
                    "planner": ["given", "greedy", "sweep"][st["planner_used"]], "n_slices": st["n_slices"],
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),

@@ -117,6 +117,8 @@ typedef struct {
                              in shared memory instead of B^T in tensor memory;
                              [2] = 1: launch kernels one by one instead of
                              replaying one captured CUDA graph per step;
+                             [3] = 1: tensor-core contractions gather A with
+                             plain loads even where TMA boxes could load it;
                              others 0 */
 } xeb_plan_opts;
 
@@ -135,7 +137,9 @@ typedef struct {
     uint64_t n_slices;          /* 2^n_sliced                                     */
     int n_gemm_ops, n_permute_ops;
     int planner_used;
-    int reserved[5];
+    int n_tc_launches;          /* tensor-core contractions per slice (after bind) */
+    int n_tc_tma;               /* ... of which load A with TMA boxes             */
+    int reserved[3];
 } xeb_stats;
 
 /* Default options (FP32, AUTO planner, 64 GiB budget). */

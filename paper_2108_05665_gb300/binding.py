@@ -66,7 +66,8 @@ class xeb_stats(ctypes.Structure):
                 ("permute_elems_per_slice", ctypes.c_double), ("objective", ctypes.c_double),
                 ("arena_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("n_slices", ctypes.c_uint64), ("n_gemm_ops", ctypes.c_int), ("n_permute_ops", ctypes.c_int),
-                ("planner_used", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("planner_used", ctypes.c_int), ("n_tc_launches", ctypes.c_int), ("n_tc_tma", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}

@@ -41,11 +41,16 @@ constexpr int GK_TC = 100;   // tcgen05 split-precision kernel, split W in smem 
 constexpr int GK_TC2 = 101;  // tcgen05 split-precision kernel, W^T in tensor memory (tc_gemm2.cu)
 
 struct GemmLaunch {
+    CUtensorMap tmap;  // A of a TMA-mode tensor-core launch (64-byte aligned)
     int kernel;
     xebk::GemmDesc d;
     xebk::StreamDesc s;
     xebk::TcDesc tc;
 };
+
+// Result bits below this C address bit are kept inside one tensor-core tile,
+// so every 32-byte sector of C is written whole by a single tile.
+constexpr int kTileLowCBits = 3;
 
 // Tensor-core eligibility and descriptor of a contraction (one key, 128-row
 // tiles, 16 <= K, N <= 64 complex, tile offsets within 32 bits).
@@ -59,13 +64,12 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits, bool tmem_variant) {
     t.n_chunks = t.K2 / 32;
     t.tmem_cols = 4 * t.N2;  // 2 buffers x (big, small) accumulators
     // rows of a tile: for the tensor-memory kernel the rows whose output bits
-    // are lowest (legs the parent sums) come first so every tile writes whole
-    // contiguous runs; then the lowest remaining rows
+    // are below kTileLowCBits come first so every tile writes whole sectors;
+    // then the lowest remaining rows
     std::vector<int> tile_rows;
     if (tmem_variant) {
-        const int n_low = int(op.c_hint.size());
         for (size_t i = 0; i < op.a_pos_m.size(); ++i)
-            if (op.c_pos_m[i] < n_low) tile_rows.push_back(int(i));
+            if (op.c_pos_m[i] < kTileLowCBits) tile_rows.push_back(int(i));
         for (size_t i = 0; i < op.a_pos_m.size() && int(tile_rows.size()) < row_bits; ++i)
             if (std::find(tile_rows.begin(), tile_rows.end(), int(i)) == tile_rows.end()) tile_rows.push_back(int(i));
         if (int(tile_rows.size()) != row_bits) return false;
@@ -119,7 +123,65 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits, bool tmem_variant) {
     t.nbn = int(op.b_pos_n.size());
     for (int i = 0; i < t.nbk; ++i) t.bpk[i] = int8_t(op.b_pos_k[i]);
     for (int i = 0; i < t.nbn; ++i) t.bpn[i] = int8_t(op.b_pos_n[i]);
+    // TMA mode (candidate; the tensor map is encoded at bind): A is a
+    // row-major [M][K] matrix and the tile's lowest >= 3 row bits are the
+    // matrix's lowest rows, so a chunk is a few boxes of >= 8 consecutive rows
+    t.tma = 0;
+    if (tmem_variant && op.M <= (int64_t(1) << 31)) {
+        const int nak = int(op.a_pos_k.size());
+        bool row_major = true;
+        for (int i = 0; i < nak; ++i) row_major = row_major && op.a_pos_k[i] == i;
+        for (size_t i = 0; i < op.a_pos_m.size(); ++i) row_major = row_major && op.a_pos_m[i] == nak + int(i);
+        int a = 0;
+        while (a < row_bits && tile_rows[a] == a) ++a;
+        if (row_major && a >= 3) {
+            t.tma = 1;
+            t.box_log2 = a;
+            t.row_shift = nak;
+            for (int j = 0; j < (1 << (row_bits - a)); ++j) {
+                int64_t y = 0;
+                for (int b = 0; b < row_bits - a; ++b)
+                    if ((j >> b) & 1) y |= int64_t(1) << tile_rows[a + b];
+                t.box_y[j] = int32_t(y);
+            }
+        }
+    }
     return true;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return EncodeTiledFn(nullptr);
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of a TMA-mode launch's A operand: [M rows][2K floats], boxes of
+// 32 floats (one 128-byte swizzle atom) x 2^box_log2 rows, 128-byte swizzle.
+// False (the launch then gathers with plain loads) if the base is not 16-byte
+// aligned or the driver refuses the map.
+bool encode_a_map(const xebk::TcDesc& t, const float2* arena, CUtensorMap& map) {
+    const float2* base = arena + t.a_off;
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+    EncodeTiledFn fn = encode_tiled_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {cuuint64_t(t.K2), cuuint64_t(t.M)};
+    const cuuint64_t strides[1] = {cuuint64_t(t.K2) * 4};
+    const cuuint32_t box[2] = {32u, cuuint32_t(1u << t.box_log2)};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Tile shape of the streaming kernel for a contraction, or false if the
@@ -523,6 +585,12 @@ extern "C" xeb_status xeb_plan_stats(xeb_plan_s* p, xeb_stats* s) {
         else ++s->n_permute_ops;
     }
     s->planner_used = p->planner_used;
+    for (size_t i = 0; i < p->gemms.size() && i < p->prog.ops.size(); ++i)
+        if (const GemmLaunch& g = p->gemms[i];
+            p->prog.ops[i].kind != OP_PERM && (g.kernel == GK_TC || g.kernel == GK_TC2)) {
+            ++s->n_tc_launches;
+            s->n_tc_tma += g.tc.tma != 0;
+        }
     return XEB_OK;
 }
 
@@ -776,6 +844,10 @@ void build_launches(xeb_plan_s* p) {
                 g.tc.c_off = d.c_off;
                 g.tc.wimg = reinterpret_cast<float*>(tables + p->t_wimg);
                 g.tc.err = reinterpret_cast<int32_t*>(tables + p->t_err);
+                std::memset(&g.tmap, 0, sizeof(g.tmap));
+                if (g.tc.tma && (p->opts.reserved[3] == 1 ||
+                                 !encode_a_map(g.tc, reinterpret_cast<const float2*>(p->ws + p->off_arena), g.tmap)))
+                    g.tc.tma = 0;
             } else if (stream_tile(op, p->elem, g.s)) g.kernel = xebk::GK_STREAM;
             else if (op.N == 1) g.kernel = xebk::GK_GEMV;
             else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;
@@ -871,7 +943,7 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 if (t.pos[i] < 0 || t.pos[i] >= op.a_rank) { why = "tensor-core tile positions"; return false; }
             if (p->gemms[i].kernel == GK_TC2) {
                 const int rc = g.nam + g.nbn;
-                if (t.n_ext + row_bits != g.nam || t.Tst != row_bits + g.nbn || (1 << (t.Tst > 5 ? t.Tst - 5 : 0)) > 256) {
+                if (t.n_ext + row_bits != g.nam || t.Tst != row_bits + g.nbn || t.Tst < 11 || t.Tst > 16) {
                     why = "tensor-core result tile of node " + std::to_string(op.node);
                     return false;
                 }
@@ -887,6 +959,21 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 if (!inside(op.a_buf, t.a_off, t.a_off + ahi + thi + t.chunk_off[t.n_chunks - 1])) {
                     why = "tensor-core operand rows of node " + std::to_string(op.node);
                     return false;
+                }
+                if (t.tma) {  // TMA boxes: rows y .. y + 2^box_log2 - 1 of an [M][K] matrix inside A's buffer
+                    bool bad = t.box_log2 < 3 || t.box_log2 > row_bits || t.row_shift != int(op.a_pos_k.size()) ||
+                               !inside(op.a_buf, t.a_off, t.a_off + g.M * g.K - 1);
+                    int64_t yext = 0;
+                    for (int i2 = 0; i2 < t.n_ext && !bad; ++i2) {
+                        bad = t.ext_apos[i2] < t.row_shift;
+                        if (!bad) yext |= int64_t(1) << (t.ext_apos[i2] - t.row_shift);
+                    }
+                    for (int j = 0; j < (1 << (row_bits - t.box_log2)) && !bad; ++j)
+                        bad = t.box_y[j] < 0 || yext + t.box_y[j] + (int64_t(1) << t.box_log2) > g.M;
+                    if (bad) {
+                        why = "tensor-core TMA boxes of node " + std::to_string(op.node);
+                        return false;
+                    }
                 }
             }
         }
@@ -949,7 +1036,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                         XEB_CUDA(xebk::launch_tc_gemm(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st));
                 } else if (g.kernel == GK_TC2) {
                     if constexpr (sizeof(T) == 8)
-                        XEB_CUDA(xebk::launch_tc_gemm2(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st));
+                        XEB_CUDA(xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st));
                 } else if (g.kernel == xebk::GK_STREAM) {
                     XEB_CUDA(xebk::launch_gemm_stream<T>(g.d, g.s, arena, st));
                 } else {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace xebk {
@@ -107,6 +108,12 @@ struct TcDesc {
     int8_t st_pos[16], st_idx[16];
     float* wimg;          // scratch: split, swizzled image of the real-expanded B
     int32_t* err;         // error word (timeouts)
+    // (tensor-memory variant, TMA mode) A is a row-major [M][K] matrix; a
+    // chunk is 128 >> box_log2 boxes of 32 floats x 2^box_log2 consecutive
+    // rows; box j starts box_y[j] rows above the tile's base row, and an
+    // outside-tile A address bit p is row bit p - row_shift
+    int tma, box_log2, row_shift;
+    int32_t box_y[16];
 };
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 size_t tc_wimg_floats(const TcDesc& t);
@@ -133,7 +140,8 @@ cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStrea
 cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);
 // Variant with W^T in tensor memory and a deep cp.async ring (64-row tiles,
 // tile bits = 6 row bits + 4 k bits).
-cudaError_t launch_tc_gemm2(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);
+// tmap: 2-D tensor map of A (used when t.tma != 0)
+cudaError_t launch_tc_gemm2(const TcDesc& t, const CUtensorMap& tmap, float2* arena, int n_sms, cudaStream_t st);
 cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k,
                               double2* amps, double* partials, int n_blocks, double* result,
                               int n_qubits, cudaStream_t st);

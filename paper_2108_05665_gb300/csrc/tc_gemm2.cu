@@ -11,10 +11,11 @@
 // W^T (big and small, <= 128 x 128 floats each) is written once per CTA into
 // tensor memory and serves as the MMA's A operand; the state rows are the
 // shared-memory B operand (K-major, 128-byte swizzle), so shared memory holds
-// only a deep ring of state chunks.  The producer warps gather state elements
-// with cp.async straight into the ring (the k legs of a contraction sit at
-// arbitrary address bits), and split each chunk into big/small in place when
-// its copies have landed.  One thread issues the MMAs; four epilogue warps
+// only a ring of split state chunks.  Eight producer warps gather state
+// elements (the k legs of a contraction sit at arbitrary address bits) with
+// the loads of four chunks in flight per thread in registers, and write each
+// chunk split into big/small into its ring stage.  One thread issues the
+// MMAs; four epilogue warps
 // read D^T from tensor memory (lane = output column), transpose it through a
 // padded shared buffer and write whole rows of C.
 //
@@ -32,18 +33,31 @@ namespace {
 constexpr int kRows = 128;           // state rows per tile (UMMA N)
 constexpr int kM = 128;              // W^T rows (UMMA M), N2 padded to 128
 constexpr int kChunk = 32;           // floats of K' per chunk (one swizzle atom)
-constexpr int kRing = 4;             // chunk stages (16 KB big + 16 KB small each)
-constexpr int kProdWarps = 4;
-constexpr int kProd = 32 * kProdWarps;            // 128 producer threads
-constexpr int kEpiWarp0 = kProdWarps;             // warps 4-7
-constexpr int kMmaWarp = kProdWarps + 4;          // warp 8
-constexpr int kThreads = 32 * (kProdWarps + 5);   // 288
-constexpr int kPerThread = kRows * 16 / kProd;    // 16 complex elements per producer per chunk
-constexpr int kRowBits = 7;
-constexpr int kTab = 256;                         // result-tile table entries
-constexpr int kStageBytes = 2 * kRows * 128;      // big + small, 16 KB each
-constexpr int kCStride = 132;                     // floats per staged output row
+// Warp roles (14 warps).  Gather mode: warps 0-7 gather A, 8-11 epilogue.
+// TMA mode: warps 0-3 split landed chunks, 4-11 epilogue (two warps per
+// tensor-memory lane quarter, each with half the tile rows), 13 issues the
+// TMA loads.  Warp 12 issues the MMAs in both modes.
+constexpr int kMmaWarp = 12;
+constexpr int kTmaWarp = 13;
+constexpr int kThreads = 32 * 14;                 // 448
+template <bool kTma>
+__host__ __device__ constexpr int prod_warps() { return kTma ? 4 : 8; }
+template <bool kTma>
+__host__ __device__ constexpr int epi_warps() { return kTma ? 8 : 4; }
+constexpr int kProd = 32 * 8;                     // gather mode: 256 producer threads
+constexpr int kPerThread = kRows * 16 / kProd;    // gather mode: 8 complex elements per producer per chunk
+constexpr int kLook = 4;                          // gather mode: chunks of loads in flight per producer (registers)
+constexpr int kStageBytes = 2 * kRows * 128;      // operand stage: big + small, 16 KB each
+constexpr int kRawBytes = kRows * 128;            // TMA mode: raw stage, 16 KB
+constexpr int kRingGather = 4;                    // operand stages, gather mode
+constexpr int kRingTma = 3;                       // operand stages, TMA mode
+constexpr int kRaw = 4;                           // raw stages, TMA mode (64 KB of loads in flight)
+constexpr int kCStride = 130;                     // floats per staged output row
 constexpr uint32_t kTmemCols = 512;
+template <bool kTma>
+__host__ __device__ constexpr int op_stages() { return kTma ? kRingTma : kRingGather; }
+template <bool kTma>
+constexpr size_t ring_bytes() { return (kTma ? size_t(kRaw) * kRawBytes : 0) + size_t(op_stages<kTma>()) * kStageBytes; }
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -80,11 +94,33 @@ __device__ bool bar_wait(uint64_t* b, uint32_t par, int32_t* err, int code) {
         }
     }
 }
+// bounded wait that ignores the error word (waiting for copies in flight)
+__device__ void bar_wait_drain(uint64_t* b, uint32_t par) {
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 0;; ++i) {
+        if (bar_try(b, par)) return;
+        if ((i & 255) == 255 && gtimer() - t0 > kWaitNs) return;
+    }
+}
+__device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// 2-D tiled TMA load (x = floats, y = rows) completing on mbarrier b
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(b))
+        : "memory");
+}
 __device__ __forceinline__ uint32_t swz(uint32_t byte) { return byte ^ (((byte >> 7) & 7u) << 4); }
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
+}
+__device__ __forceinline__ float4 tf32_rn4(float4 v) {
+    return make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
 }
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
@@ -104,14 +140,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* b) {
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void cp8(void* s, const void* g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
+// 32 lanes x 32 columns of tensor memory into registers (no wait)
 __device__ __forceinline__ void tm_ld32(uint32_t ta, float* v) {
     uint32_t r[32];
     asm volatile(
@@ -122,10 +151,10 @@ __device__ __forceinline__ void tm_ld32(uint32_t ta, float* v) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(ta));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tm_st32(uint32_t ta, const float* v) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
@@ -144,35 +173,46 @@ __device__ __forceinline__ void tm_st32(uint32_t ta, const float* v) {
         : "memory");
 }
 struct Sm2 {
-    uint64_t full[kRing], empty[kRing], tfull[2], tempty[2], wready, drain, epi;
-    int64_t hi_glob[kTab];
-    int32_t hi_slot[kTab];
-    uint32_t tmem;
+    uint64_t full[kRingGather], empty[kRingGather], rfull[kRaw], rempty[kRaw], tfull[2], tempty[2], wready, drain, epi;
+    uint32_t tmem, pad;
 };
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant__ TcDesc t, float2* __restrict__ arena) {
+template <bool kTma>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm2(const __grid_constant__ TcDesc t, const __grid_constant__ CUtensorMap tmap, float2* __restrict__ arena) {
+    constexpr int kRing = op_stages<kTma>();
+    constexpr int kProdWarps = prod_warps<kTma>();
+    constexpr int kProdT = 32 * kProdWarps;        // threads that fill the operand ring
+    constexpr int kEpiWarps = epi_warps<kTma>();
+    constexpr int kEpiWarp0 = kProdWarps;
+    constexpr int kEpiT = 32 * kEpiWarps;
     extern __shared__ __align__(1024) unsigned char raw2[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw2) + 1023) & ~uintptr_t(1023));
-    unsigned char* ring = sm;                                         // kRing x (big 8 KB | small 8 KB)
-    float* cst = reinterpret_cast<float*>(sm + kRing * kStageBytes);  // kRows x kCStride
+    unsigned char* rawr = sm;                                          // TMA mode: kRaw x 16 KB
+    unsigned char* ring = sm + (kTma ? kRaw * kRawBytes : 0);          // kRing x (big 16 KB | small 16 KB)
+    float* cst = reinterpret_cast<float*>(ring + kRing * kStageBytes);  // kRows x kCStride
     Sm2* S = reinterpret_cast<Sm2*>(cst + kRows * kCStride);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = t.M / kRows;
     const int nch = t.n_chunks;
     if (tid == 0) {
         for (int s = 0; s < kRing; ++s) {
-            bar_init(&S->full[s], kProd);
+            bar_init(&S->full[s], kProdT);
             bar_init(&S->empty[s], 1);
+        }
+        for (int s = 0; s < kRaw; ++s) {
+            bar_init(&S->rfull[s], 1);
+            bar_init(&S->rempty[s], kProdT);
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(&S->tfull[b], 1);
-            bar_init(&S->tempty[b], 128);
+            bar_init(&S->tempty[b], kEpiT);
         }
-        bar_init(&S->wready, 128);
+        bar_init(&S->wready, kEpiT);
         bar_init(&S->drain, 1);
-        bar_init(&S->epi, 128);
+        bar_init(&S->epi, kEpiT);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
@@ -187,8 +227,73 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
     const uint32_t tmem = S->tmem;
     const uint32_t w_big = tmem, w_small = tmem + 128;
 
-    if (warp < kProdWarps) {
-        // ---------------- producers: gather (cp.async) and split in place ----------------
+    if (kTma && warp < kProdWarps) {
+        // ---------------- TMA mode: split landed raw chunks into the operand ring ----------------
+        // raw and operand stages are 1024-byte aligned, so the 128-byte swizzle
+        // the TMA applied is the layout the MMA reads: the split is a linear copy
+        const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const int64_t total = my_tiles * nch;
+        for (int64_t c = 0; c < total; ++c) {
+            const int s1 = int(c % kRaw), s2 = int(c % kRing);
+            if (!bar_wait(&S->rfull[s1], uint32_t(c / kRaw) & 1, t.err, 20)) break;
+            if (!bar_wait(&S->empty[s2], (uint32_t(c / kRing) & 1) ^ 1, t.err, 11)) break;
+            const float4* src = reinterpret_cast<const float4*>(rawr + s1 * kRawBytes);
+            float4* db = reinterpret_cast<float4*>(ring + s2 * kStageBytes);
+            float4* ds = db + kRawBytes / 16;
+            constexpr int kV = kRawBytes / 16 / kProdT;  // float4 per thread
+            float4 v[kV];
+#pragma unroll
+            for (int i = 0; i < kV; ++i) v[i] = src[tid + kProdT * i];
+#pragma unroll
+            for (int i = 0; i < kV; ++i) {
+                const float4 b = tf32_rn4(v[i]);
+                db[tid + kProdT * i] = b;
+                ds[tid + kProdT * i] = tf32_rn4(make_float4(v[i].x - b.x, v[i].y - b.y, v[i].z - b.z, v[i].w - b.w));
+            }
+            bar_arrive(&S->rempty[s1]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bar_arrive(&S->full[s2]);
+        }
+    } else if (kTma && warp == kTmaWarp) {
+        // ---------------- TMA mode: one thread issues the box loads ----------------
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+            const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+            const int64_t total = my_tiles * nch;
+            const int nbox = kRows >> t.box_log2;
+            const int brow = (1 << t.box_log2) * 128;  // bytes of one box in shared memory
+            auto ybase = [&](int64_t tile) {
+                int64_t y = 0;
+                for (int i = 0; i < t.n_ext; ++i)
+                    if ((tile >> i) & 1) y |= int64_t(1) << (t.ext_apos[i] - t.row_shift);
+                return y;
+            };
+            int64_t tile = blockIdx.x, c = 0;
+            int cin = 0;
+            int64_t y0 = ybase(tile);
+            for (; c < total; ++c) {
+                const int s = int(c % kRaw);
+                if (!bar_wait(&S->rempty[s], (uint32_t(c / kRaw) & 1) ^ 1, t.err, 18)) break;
+                bar_expect_tx(&S->rfull[s], kRawBytes);
+                unsigned char* dst = rawr + s * kRawBytes;
+                for (int j = 0; j < nbox; ++j)
+                    tma_load_2d(dst + j * brow, &tmap, kChunk * cin, int(y0 + t.box_y[j]), &S->rfull[s]);
+                if (++cin == nch) {
+                    cin = 0;
+                    tile += gridDim.x;
+                    y0 = tile < n_tiles ? ybase(tile) : 0;
+                }
+            }
+            // the CTA must not exit with copies in flight: wait (bounded) for the last ones
+            for (int64_t d = c > kRaw ? c - kRaw : 0; d < c; ++d)
+                bar_wait_drain(&S->rfull[d % kRaw], uint32_t(d / kRaw) & 1);
+        }
+        __syncwarp();
+    } else if (!kTma && warp < kProdWarps) {
+        // ---------------- producers: gather into registers, split into the ring ----------------
+        // Each thread keeps the loads of kLook chunks in flight in registers;
+        // chunk c is split into big/small straight into its ring stage once
+        // the stage is free, then the loads of chunk c + kLook are issued.
         int32_t off[kPerThread];
         uint32_t pos[kPerThread];
 #pragma unroll
@@ -207,49 +312,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
         }
         const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
         const int64_t total = my_tiles * nch;
-        constexpr int D = kRing - 2;   // chunks whose copies are in flight ahead of the split
+        // issue-side cursor (chunks are issued in order)
+        int64_t ld_tile = blockIdx.x;
+        int ld_c = 0;
+        auto tile_base = [&](int64_t tile) {
+            int64_t b = 0;
+            for (int i = 0; i < t.n_ext; ++i)
+                if ((tile >> i) & 1) b |= int64_t(1) << t.ext_apos[i];
+            return b;
+        };
+        const float2* Arow = arena + t.a_off + tile_base(ld_tile) + t.chunk_off[0];
+        float2 buf[kLook][kPerThread];
+#define XEB_TC2_ISSUE(U)                                                                   \
+    do {                                                                                   \
+        _Pragma("unroll") for (int j = 0; j < kPerThread; ++j) buf[U][j] = __ldg(Arow + off[j]); \
+        if (++ld_c == nch) {                                                               \
+            ld_c = 0;                                                                      \
+            ld_tile += gridDim.x;                                                          \
+            Arow = arena + t.a_off + (ld_tile < n_tiles ? tile_base(ld_tile) : 0) + t.chunk_off[0]; \
+        } else {                                                                           \
+            Arow += t.chunk_off[ld_c] - t.chunk_off[ld_c - 1];                             \
+        }                                                                                  \
+    } while (0)
+#pragma unroll
+        for (int u = 0; u < kLook; ++u)
+            if (u < total) XEB_TC2_ISSUE(u);
         bool ok = true;
-        int64_t tile_of = -1, base = 0;
-        int c = 0;
-        int64_t tcur = blockIdx.x;
-        for (int64_t it = 0; it < total + D && ok; ++it) {
-            if (it < total) {
-                const int s = int(it % kRing);
-                const uint32_t use = uint32_t(it / kRing);
-                if (!bar_wait(&S->empty[s], (use & 1) ^ 1, t.err, 11)) { ok = false; break; }
-                if (tile_of != tcur) {
-                    tile_of = tcur;
-                    base = 0;
-                    for (int i = 0; i < t.n_ext; ++i)
-                        if ((tcur >> i) & 1) base |= int64_t(1) << t.ext_apos[i];
-                }
-                const float2* A = arena + t.a_off + base + t.chunk_off[c];
-                unsigned char* sb = ring + s * kStageBytes;
+        for (int64_t c0 = 0; c0 < total && ok; c0 += kLook) {
 #pragma unroll
-                for (int j = 0; j < kPerThread; ++j) cp8(sb + pos[j], A + off[j]);
-                if (++c == nch) { c = 0; tcur += gridDim.x; }
-            }
-            cp_commit();
-            if (it >= D) {
-                // copies of chunk it-D have landed: split big/small in place
-                cp_wait<D>();
-                const int64_t jt = it - D;
-                const int s = int(jt % kRing);
-                unsigned char* sb = ring + s * kStageBytes;
+            for (int u = 0; u < kLook; ++u) {
+                const int64_t c = c0 + u;
+                if (c < total && ok) {
+                    const int s = int(c % kRing);
+                    const uint32_t use = uint32_t(c / kRing);
+                    if (!bar_wait(&S->empty[s], (use & 1) ^ 1, t.err, 11)) {
+                        ok = false;
+                    } else {
+                        unsigned char* sb = ring + s * kStageBytes;
 #pragma unroll
-                for (int j = 0; j < kPerThread; ++j) {
-                    float2* pb = reinterpret_cast<float2*>(sb + pos[j]);
-                    const float2 v = *pb;
-                    const float bx = tf32_rn(v.x), by = tf32_rn(v.y);
-                    *pb = make_float2(bx, by);
-                    *reinterpret_cast<float2*>(sb + kRows * 128 + pos[j]) =
-                        make_float2(tf32_rn(v.x - bx), tf32_rn(v.y - by));
+                        for (int j = 0; j < kPerThread; ++j) {
+                            const float2 v = buf[u][j];
+                            const float bx = tf32_rn(v.x), by = tf32_rn(v.y);
+                            *reinterpret_cast<float2*>(sb + pos[j]) = make_float2(bx, by);
+                            *reinterpret_cast<float2*>(sb + kRows * 128 + pos[j]) =
+                                make_float2(tf32_rn(v.x - bx), tf32_rn(v.y - by));
+                        }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        bar_arrive(&S->full[s]);
+                        if (c + kLook < total) XEB_TC2_ISSUE(u);
+                    }
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                bar_arrive(&S->full[s]);
             }
         }
-        cp_wait<0>();
+#undef XEB_TC2_ISSUE
     } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -286,9 +401,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
             bar_wait(&S->drain, 0, t.err, 15);
         }
         __syncwarp();
-    } else {
+    } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
         // ---------------- W^T into tensor memory, then the epilogue ----------------
-        const int q = warp - kEpiWarp0;          // lane quarter (warps 4..7 -> 0..3)
+        const int widx = warp - kEpiWarp0;       // 0 .. kEpiWarps - 1
+        const int q = warp & 3;                  // tensor-memory lane quarter of this warp
+        const int half = widx >> 2;              // which share of columns / rows
+        constexpr int kShares = kEpiWarps / 4;
         const int np = q * 32 + lane;            // W^T row = output column n' (0..127)
         {
             const int n = np >> 1, cpart = np & 1;
@@ -298,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
                 for (int i = 0; i < t.nbn; ++i)
                     if ((n >> i) & 1) noff |= int64_t(1) << t.bpn[i];
             const float2* B = arena + t.b_off;
-            for (int c0 = 0; c0 < t.K2; c0 += 32) {
+            for (int c0 = 32 * half; c0 < t.K2; c0 += 32 * kShares) {
                 float vb[32], vs[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
@@ -324,36 +442,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
         }
         uint32_t tc = 0, ep = 0;
         const uint32_t lanes = uint32_t(q * 32) << 16;
-        const int etid = tid - 32 * kEpiWarp0;   // 0..127
-        // result tile element e (bits in ascending C address) -> staging slot
-        // and C offset; split as e = e_hi * 32 + lane: the lane part once per
-        // thread, the e_hi part in a per-CTA table
+        // Result tile element e (its bits in ascending C address order) =
+        // h * 32 + lane.  Its C offset and staging slot are sums of one
+        // increment per set bit, so each warp owns a contiguous block of h and
+        // keeps the increments of the block's low 3 bits in registers: eight
+        // independent staging loads and stores per group, no table lookups.
+        auto ginc = [&](int i) { return int64_t(1) << t.st_pos[i]; };
+        auto sinc = [&](int i) {
+            return ((t.st_is_n >> i) & 1) ? (1 << t.st_idx[i]) : (1 << t.st_idx[i]) * (kCStride / 2);
+        };
         int lo_slot = 0;
         int64_t lo_glob = 0;
-        {
-            int r = 0, n = 0;
-            for (int i = 0; i < 5 && i < t.Tst; ++i) {
-                const int bit = (lane >> i) & 1;
-                if (!bit) continue;
-                if ((t.st_is_n >> i) & 1) n |= 1 << t.st_idx[i];
-                else r |= 1 << t.st_idx[i];
-                lo_glob |= int64_t(1) << t.st_pos[i];
+        for (int i = 0; i < 5; ++i)  // Tst >= 11 (7 row bits + >= 4 column bits)
+            if ((lane >> i) & 1) {
+                lo_glob += ginc(i);
+                lo_slot += sinc(i);
             }
-            lo_slot = r * (kCStride / 2) + n;
-        }
-        const int n_hi = t.Tst > 5 ? 1 << (t.Tst - 5) : 1;
-        for (int h = etid; h < n_hi; h += 128) {  // n_hi <= kTab
-            int r = 0, n = 0;
-            int64_t g = 0;
-            for (int i = 5; i < t.Tst; ++i) {
-                if (!((h >> (i - 5)) & 1)) continue;
-                if ((t.st_is_n >> i) & 1) n |= 1 << t.st_idx[i];
-                else r |= 1 << t.st_idx[i];
-                g |= int64_t(1) << t.st_pos[i];
+        constexpr int kWB = kEpiWarps == 8 ? 3 : 2;  // log2(epilogue warps)
+        const int hb = t.Tst - 5;                    // bits of h
+        const int qb = hb < kWB ? hb : kWB;          // bits selecting the warp's block
+        const int wb = hb - qb;                      // bits inside the block
+        const int lb = wb < 3 ? wb : 3;              // of which held in registers
+        const bool e_active = widx < (1 << qb);
+        int64_t gq = lo_glob;
+        int sq = lo_slot;
+        for (int i = 0; i < qb; ++i)
+            if ((widx >> i) & 1) {
+                gq += ginc(5 + wb + i);
+                sq += sinc(5 + wb + i);
             }
-            S->hi_slot[h] = r * (kCStride / 2) + n;
-            S->hi_glob[h] = g;
+        int64_t g8[8];
+        int s8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            g8[j] = 0;
+            s8[j] = 0;
+            for (int b = 0; b < lb; ++b)
+                if ((j >> b) & 1) {
+                    g8[j] += ginc(5 + b);
+                    s8[j] += sinc(5 + b);
+                }
         }
+        const int nlo = 1 << lb, nmid = 1 << (wb - lb);
         // bounded sync of the four epilogue warps (an aborting warp cannot
         // leave the others blocked)
         auto epi_sync = [&]() {
@@ -362,31 +492,51 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
             ++ep;
             return ok;
         };
-        bool table_ok = __all_sync(0xffffffffu, epi_sync());  // table visible to all four warps
-        for (int64_t tile = blockIdx.x; tile < n_tiles && table_ok; tile += gridDim.x, ++tc) {
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tc) {
             const uint32_t b = 0, ub = tc;
             const bool got = bar_wait(&S->tfull[b], ub & 1, t.err, 16);
             if (!__all_sync(0xffffffffu, got)) break;
             fence_after();
-            // D^T: lane = output column np, column = tile row
+            // D^T: lane = output column np, column = tile row; tensor memory is
+            // released for the next tile's MMAs once the last load has landed
             const uint32_t db = tmem + 256;
-            for (int r0 = 0; r0 < kRows; r0 += 32) {
+            constexpr int kMyRows = kRows / kShares;
+            for (int r0 = half * kMyRows; r0 < (half + 1) * kMyRows; r0 += 32) {
                 float v[32], w[32];
                 tm_ld32(db + lanes + uint32_t(r0), v);
                 tm_ld32(db + lanes + kRows + uint32_t(r0), w);
+                tm_wait_ld();
+                if (r0 == (half + 1) * kMyRows - 32) {
+                    fence_before();
+                    bar_arrive(&S->tempty[b]);
+                }
 #pragma unroll
                 for (int i = 0; i < 32; ++i) cst[(r0 + i) * kCStride + np] = v[i] + w[i];
             }
-            fence_before();
-            bar_arrive(&S->tempty[b]);
             if (!__all_sync(0xffffffffu, epi_sync())) break;
-            // the tile's results in ascending C address order (contiguous runs)
             int64_t cbase = 0;
             for (int i = 0; i < t.n_ext; ++i)
                 if ((tile >> i) & 1) cbase |= int64_t(1) << t.ext_cpos[i];
-            float2* C = arena + t.c_off + cbase + lo_glob;
+            float2* C = arena + t.c_off + cbase;
             const float2* st2 = reinterpret_cast<const float2*>(cst);
-            for (int h = q; h < n_hi; h += 4) C[S->hi_glob[h]] = st2[S->hi_slot[h] + lo_slot];
+            if (e_active) {
+                for (int jm = 0; jm < nmid; ++jm) {
+                    int64_t gm = gq;
+                    int sm2 = sq;
+                    for (int bb = 0; bb < wb - lb; ++bb)
+                        if ((jm >> bb) & 1) {
+                            gm += ginc(5 + lb + bb);
+                            sm2 += sinc(5 + lb + bb);
+                        }
+                    float2 v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j < nlo) v[j] = st2[sm2 + s8[j]];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j < nlo) C[gm + g8[j]] = v[j];
+                }
+            }
             if (!__all_sync(0xffffffffu, epi_sync())) break;
         }
     }
@@ -398,11 +548,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm2(const __grid_constant_
     }
 }
 
-// 1024 bytes of alignment slack + ring + output staging + barriers/tables
-size_t tc2_smem_bytes() {
-    return 1024 + size_t(kRing) * kStageBytes + size_t(kRows) * kCStride * 4 + sizeof(Sm2);
+// 1024 bytes of alignment slack + rings + output staging + barriers/tables
+template <bool kTma>
+constexpr size_t tc2_smem() {
+    return 1024 + ring_bytes<kTma>() + size_t(kRows) * kCStride * 4 + sizeof(Sm2);
 }
-static_assert(sizeof(Sm2) % 8 == 0 && 1024 + kRing * kStageBytes + kRows * kCStride * 4 + sizeof(Sm2) <= 232448,
+static_assert(sizeof(Sm2) % 8 == 0 && tc2_smem<true>() <= 232448 && tc2_smem<false>() <= 232448,
               "tensor-memory contraction exceeds the shared memory of one CTA");
 
 cudaError_t prepare_tc1();
@@ -410,13 +561,18 @@ cudaError_t prepare_tc1();
 cudaError_t prepare_tc_kernels() {
     cudaError_t e = prepare_tc1();
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tc_gemm2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem_bytes()));
+    e = cudaFuncSetAttribute(k_tc_gemm2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<true>()));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tc_gemm2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<false>()));
 }
 
-cudaError_t launch_tc_gemm2(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st) {
+cudaError_t launch_tc_gemm2(const TcDesc& t, const CUtensorMap& tmap, float2* arena, int n_sms, cudaStream_t st) {
     const int64_t tiles = t.M / kRows;
     const int grid = int(tiles < n_sms ? tiles : n_sms);
-    k_tc_gemm2<<<grid, kThreads, tc2_smem_bytes(), st>>>(t, arena);
+    if (t.tma)
+        k_tc_gemm2<true><<<grid, kThreads, tc2_smem<true>(), st>>>(t, tmap, arena);
+    else
+        k_tc_gemm2<false><<<grid, kThreads, tc2_smem<false>(), st>>>(t, tmap, arena);
     return cudaGetLastError();
 }
 

@@ -195,3 +195,29 @@ def test_tf32x3_tensor_core_parity(grid4x5, planner, block, smem_w):
     # for 3xTF32 the measured bias is asserted against 2 x AMP_TOL.
     assert abs(F - xeb.fidelity(ref, 20)) < TF32_F_TOL
     plan.close()
+
+
+@pytest.mark.parametrize("block", [6, 5])
+def test_tf32x3_tma_matches_gather(grid4x5, block):
+    """Tensor-core contractions whose A operand is a row-major matrix load it
+    with TMA boxes; the plain-load gather path builds the same shared-memory
+    operands, so both give identical bits (and both meet the oracle bound)."""
+    import torch
+    circ, bits, ref = grid4x5
+    res = {}
+    for gather in (0, 1):
+        o = B.xeb_default_opts()
+        o.block_qubits = block
+        o.reserved[3] = gather
+        amps, F, plan = run(circ, bits, precision=B.XEB_PREC_TF32X3, planner=B.XEB_PLANNER_SWEEP, opts=o)
+        st = plan.stats()
+        print("block %d gather %d: tc launches %d, tma %d" % (block, gather, st["n_tc_launches"], st["n_tc_tma"]))
+        if gather:
+            assert st["n_tc_tma"] == 0
+        else:
+            assert st["n_tc_tma"] > 0
+        assert rel_err(amps, ref, 20).max() < AMP_TOL
+        res[gather] = (amps, F)
+        plan.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
