@@ -837,7 +837,8 @@ void build_launches(xeb_plan_s* p) {
                 d.n_groups = 1;
             }
             if (op.M == 1 && op.N == 1) g.kernel = xebk::GK_TAIL;
-            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc, 7, p->opts.reserved[1] != 1)) {
+            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc, p->opts.reserved[1] != 1 ? xebk::kTc2RowBits : 7,
+                                                                  p->opts.reserved[1] != 1)) {
                 g.kernel = p->opts.reserved[1] == 1 ? GK_TC : GK_TC2;
                 g.tc.a_off = d.a_off;
                 g.tc.b_off = d.b_off;
@@ -920,7 +921,7 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
         }
         if (p->gemms[i].kernel == GK_TC || p->gemms[i].kernel == GK_TC2) {
             const xebk::TcDesc& t = p->gemms[i].tc;
-            const int row_bits = 7;
+            const int row_bits = p->gemms[i].kernel == GK_TC2 ? xebk::kTc2RowBits : 7;
             if (t.M != g.M || t.M % (int64_t(1) << row_bits) != 0 || t.K2 != 2 * g.K || t.N2 != 2 * g.N ||
                 t.K2 % 32 != 0 || t.N2 % 32 != 0 || t.N2 > 128 || t.K2 > 128 || t.n_chunks * 32 != t.K2 ||
                 t.n_chunks > 4 || t.T != row_bits + 4 || g.kv != 1 ||
@@ -943,7 +944,8 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 if (t.pos[i] < 0 || t.pos[i] >= op.a_rank) { why = "tensor-core tile positions"; return false; }
             if (p->gemms[i].kernel == GK_TC2) {
                 const int rc = g.nam + g.nbn;
-                if (t.n_ext + row_bits != g.nam || t.Tst != row_bits + g.nbn || t.Tst < 11 || t.Tst > 16) {
+                if (t.n_ext + row_bits != g.nam || t.n_ext > 32 || t.Tst != row_bits + g.nbn || t.Tst < row_bits + 4 ||
+                    t.Tst > 16) {
                     why = "tensor-core result tile of node " + std::to_string(op.node);
                     return false;
                 }

@@ -109,13 +109,14 @@ struct TcDesc {
     float* wimg;          // scratch: split, swizzled image of the real-expanded B
     int32_t* err;         // error word (timeouts)
     // (tensor-memory variant, TMA mode) A is a row-major [M][K] matrix; a
-    // chunk is 128 >> box_log2 boxes of 32 floats x 2^box_log2 consecutive
-    // rows; box j starts box_y[j] rows above the tile's base row, and an
-    // outside-tile A address bit p is row bit p - row_shift
+    // chunk is 2^(kTc2RowBits - box_log2) boxes of 32 floats x 2^box_log2
+    // consecutive rows; box j starts box_y[j] rows above the tile's base row,
+    // and an outside-tile A address bit p is row bit p - row_shift
     int tma, box_log2, row_shift;
     int32_t box_y[16];
 };
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
+constexpr int kTc2RowBits = 7;               // tensor-memory variant: 128 state rows per tile
 size_t tc_wimg_floats(const TcDesc& t);
 
 // ---- launch wrappers (all asynchronous on `st`) --------------------------------

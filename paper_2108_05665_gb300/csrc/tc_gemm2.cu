@@ -31,6 +31,7 @@ namespace xebk {
 namespace {
 
 constexpr int kRows = 128;           // state rows per tile (UMMA N)
+static_assert(kRows == 1 << kTc2RowBits, "tile rows must match the host tiling");
 constexpr int kM = 128;              // W^T rows (UMMA M), N2 padded to 128
 constexpr int kChunk = 32;           // floats of K' per chunk (one swizzle atom)
 // Warp roles (14 warps).  Gather mode: warps 0-7 gather A, 8-11 epilogue.
