@@ -179,6 +179,25 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def tc_traffic_per_launch(alg_bytes):
+    """DRAM bytes per launch of the tensor-core kernel, scaled from the ncu
+    capture summarised under profiles/ (DRAM bytes per algorithmic byte);
+    None when the kernel source changed since that capture."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "paper_2108_05665_gb300", "csrc", "tc_gemm2.cu")
+    prof = os.path.join(here, "profiles", "k_tc_gemm2_grid3x9_m12_k2000_tf32x3.md")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        for line in open(prof):
+            f = line.split()
+            if len(f) == 5 and f[0] == "k_tc_gemm2" and f[1] == "dram_bytes_per_algorithmic_byte" and f[4] == sha:
+                return float(f[2]) * alg_bytes
+    except OSError:
+        pass
+    return None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,6 +319,7 @@ def main():
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
         peak = hbm
         peak_note = "measured copy bandwidth (" + pk_kind + ")"
+    traffic = tc_traffic_per_launch(d["bytes"] / d["launches"]) if name == "gemm_tc" else None
     eff_tflops = st["flops_per_slice"] * st["n_slices"] * args.steps * world / (ms_total / 1e3) / 1e12
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
     line = {
@@ -321,7 +341,10 @@ def main():
                 "d2h_bytes_per_step": 16 * k + 32},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
+                     "traffic_source": "ncu DRAM bytes per algorithmic byte of the tensor-core kernel "
+                                       "(27-qubit capture under profiles/) x this launch's algorithmic bytes"
+                     if traffic is not None else "no capture of the current kernel source",
                      "per_launch_ms": per_launch_ms,
                      "share_of_step": d["ms"] / ms_total},
         "kernels": {kname: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
