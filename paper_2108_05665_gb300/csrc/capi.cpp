@@ -243,7 +243,7 @@ struct xeb_plan_s {
     size_t bytes_total = 0;
     // offsets inside tables (bytes)
     int64_t t_trie_desc = 0, t_internal = 0, t_leaf_desc = 0, t_pi = 0, t_bits = 0, t_acc = 0, t_amps = 0,
-            t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0;
+            t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0, t_sort = 0;
     int n_sms = 152;
     int64_t tables_bytes = 0;
     std::vector<xebk::TrieDesc> trie;
@@ -445,8 +445,8 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
     if (!out) return fail(XEB_EINVAL, "out is NULL");
     *out = nullptr;
     if (k == 0 || !bitstrings) return fail(XEB_EINVAL, "need k >= 1 bitstrings");
-    if (k > size_t(xebk::kMaxTrieK))
-        return fail(XEB_EUNSUPPORTED, "k > " + std::to_string(xebk::kMaxTrieK) + " bitstrings per plan");
+    if (k > size_t(xebk::kMaxK))
+        return fail(XEB_EUNSUPPORTED, "k > " + std::to_string(xebk::kMaxK) + " bitstrings per plan");
     std::unique_ptr<xeb_plan_s> p(new xeb_plan_s());
     if (opts) p->opts = *opts;
     else xeb_default_opts(&p->opts);
@@ -699,6 +699,7 @@ void layout_device(xeb_plan_s* p) {
     p->t_result = take(64);
     p->t_err = take(16);
     p->t_wimg = take(p->opts.precision == XEB_PREC_TF32X3 ? 2 * 4 * 128 * 32 * 4 : 16);
+    p->t_sort = take(p->k > size_t(xebk::kMaxTrieK) ? int64_t(xebk::trie_sort_scratch_bytes(int(p->k))) : 16);
     p->tables_bytes = t;
     p->bytes_total = size_t(off + t);
 }
@@ -1064,9 +1065,16 @@ xeb_status build_tables(xeb_plan_s* p, cudaStream_t st) {
     char* tables = p->ws + p->off_tables;
     ProfScope ps(p, st, XEB_KC_TRIE, 0.0, double(p->k) * 8.0 * double(p->trie.size() + 1));
     const auto* tdesc = reinterpret_cast<const xebk::TrieDesc*>(tables + p->t_trie_desc);
-    XEB_CUDA(xebk::launch_trie_keys(tdesc, int(p->trie.size()), reinterpret_cast<const uint64_t*>(tables + p->t_bits),
-                                    int(p->k), reinterpret_cast<const int32_t*>(tables + p->t_pi), tables,
-                                    reinterpret_cast<int32_t*>(tables + p->t_err), st));
+    if (p->k <= size_t(xebk::kMaxTrieK))
+        XEB_CUDA(xebk::launch_trie_keys(tdesc, int(p->trie.size()),
+                                        reinterpret_cast<const uint64_t*>(tables + p->t_bits), int(p->k),
+                                        reinterpret_cast<const int32_t*>(tables + p->t_pi), tables,
+                                        reinterpret_cast<int32_t*>(tables + p->t_err), st));
+    else
+        XEB_CUDA(xebk::launch_trie_keys_large(tdesc, p->trie.data(), int(p->trie.size()),
+                                              reinterpret_cast<const uint64_t*>(tables + p->t_bits), int(p->k),
+                                              reinterpret_cast<const int32_t*>(tables + p->t_pi), tables,
+                                              tables + p->t_sort, reinterpret_cast<int32_t*>(tables + p->t_err), st));
     XEB_CUDA(xebk::launch_trie_links(tdesc, reinterpret_cast<const int*>(tables + p->t_internal),
                                      int(p->trie_internal.size()), p->max_kv, tables, st));
     p->tables_ready = true;

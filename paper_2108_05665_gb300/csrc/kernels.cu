@@ -18,6 +18,8 @@
 //      XEB F = 2^n/k sum_i p(s_i) - 1 of Eq. (1), FP64, fixed reduction order.
 #include "kernels.cuh"
 
+#include <utility>
+
 namespace xebk {
 
 // ---- complex helpers -----------------------------------------------------------
@@ -180,6 +182,176 @@ cudaError_t launch_trie_keys(const TrieDesc* d_desc, int n_nodes, const uint64_t
     while (kpad < k) kpad <<= 1;
     const size_t smem = size_t(kpad) * (sizeof(uint64_t) + sizeof(int32_t));
     k_trie_keys<<<n_nodes, 1024, smem, st>>>(d_desc, bits, k, kpad, pi, tables, err);
+    return cudaGetLastError();
+}
+
+// ---- a1 for large k: one LSD radix sort per node across CTAs ----------------------
+// Same tables as k_trie_keys (keys are ranks of the node's bit-range value),
+// for k beyond one CTA's shared memory.  Per 8-bit digit: a per-tile
+// histogram, one scan of (digit, tile) counts, and a stable scatter that ranks
+// equal digits within a warp with __match_any_sync and across warps with
+// per-warp digit counts; then run boundaries are counted per tile, scanned,
+// and every bitstring gets the rank of its run.
+constexpr int kRsThreads = 256;
+constexpr int kRsTile = 4096;   // elements per CTA tile
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_extract(const TrieDesc* desc, int node, const uint64_t* bits,
+                                                           int k, const int32_t* pi, uint64_t* keys, int32_t* vals) {
+    const int a = desc[node].a, b = desc[node].b;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const uint64_t s = bits[i];
+        uint64_t v = 0;
+        for (int t = a; t < b; ++t) v = (v << 1) | ((s >> pi[t]) & 1ull);
+        keys[i] = v;
+        vals[i] = i;
+    }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t* keys, int k, int shift, int32_t* hist,
+                                                        int nb) {
+    __shared__ int32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kRsTile;
+    for (int j = threadIdx.x; j < kRsTile; j += kRsThreads) {
+        const int i = base + j;
+        if (i < k) atomicAdd(&h[int((keys[i] >> shift) & 255u)], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];  // digit-major: scan gives stable bucket starts
+}
+
+// exclusive scan of n int32 in place, one CTA
+__global__ void __launch_bounds__(1024) k_rs_scan(int32_t* a, int n) {
+    const int chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int lo = min(n, int(threadIdx.x) * chunk), hi = min(n, lo + chunk);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += a[i];
+    int total = 0;
+    int run = block_exclusive_scan(sum, &total);
+    for (int i = lo; i < hi; ++i) {
+        const int v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* kin, const int32_t* vin, uint64_t* kout,
+                                                           int32_t* vout, int k, int shift, const int32_t* off,
+                                                           int nb) {
+    __shared__ int32_t run[256];
+    __shared__ int32_t wcnt[kRsThreads / 32][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    run[threadIdx.x] = off[threadIdx.x * nb + blockIdx.x];
+    const int base = blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsTile / kRsThreads; ++r) {
+        for (int j = threadIdx.x; j < (kRsThreads / 32) * 256; j += kRsThreads) (&wcnt[0][0])[j] = 0;
+        __syncthreads();
+        const int i = base + r * kRsThreads + threadIdx.x;   // elements in order: stable
+        const bool live = i < k;
+        const uint64_t key = live ? kin[i] : 0;
+        const int32_t val = live ? vin[i] : 0;
+        const int dg = live ? int((key >> shift) & 255u) : 256 + lane;   // dead lanes: unique non-digits
+        const unsigned same = __match_any_sync(0xffffffffu, dg);
+        const int rank_w = __popc(same & ((1u << lane) - 1u));
+        if (live && rank_w == 0) wcnt[w][dg] = __popc(same);
+        __syncthreads();
+        if (live) {
+            int pre = 0;
+            for (int ww = 0; ww < w; ++ww) pre += wcnt[ww][dg];
+            const int pos = run[dg] + pre + rank_w;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        int add = 0;
+        for (int ww = 0; ww < kRsThreads / 32; ++ww) add += wcnt[ww][threadIdx.x];
+        run[threadIdx.x] += add;
+        __syncthreads();
+    }
+}
+
+// number of run starts (key differs from its predecessor) per tile
+__global__ void __launch_bounds__(kRsThreads) k_rs_flags(const uint64_t* keys, int k, int32_t* cnt) {
+    const int base = blockIdx.x * kRsTile;
+    int c = 0;
+    for (int j = threadIdx.x; j < kRsTile; j += kRsThreads) {
+        const int i = base + j;
+        if (i < k && (i == 0 || keys[i] != keys[i - 1])) ++c;
+    }
+    int total = 0;
+    block_exclusive_scan(c, &total);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+// ranks: every bitstring gets the rank of its run; run starts write the
+// distinct value and a representative; the node's count is checked
+__global__ void __launch_bounds__(kRsThreads) k_rs_rank(const TrieDesc* desc, int node, const uint64_t* keys,
+                                                        const int32_t* vals, int k, const int32_t* cnt_off,
+                                                        char* tables, int32_t* err) {
+    const TrieDesc d = desc[node];
+    constexpr int kPer = kRsTile / kRsThreads;   // consecutive elements per thread
+    const int lo = blockIdx.x * kRsTile + threadIdx.x * kPer;
+    int c = 0;
+    for (int j = 0; j < kPer; ++j) {
+        const int i = lo + j;
+        if (i < k && (i == 0 || keys[i] != keys[i - 1])) ++c;
+    }
+    int total = 0;
+    int rank = cnt_off[blockIdx.x] + block_exclusive_scan(c, &total) - 1;
+    int32_t* key = reinterpret_cast<int32_t*>(tables + d.key_off);
+    uint64_t* uniq = reinterpret_cast<uint64_t*>(tables + d.uniq_off);
+    int32_t* rep = reinterpret_cast<int32_t*>(tables + d.rep_off);
+    for (int j = 0; j < kPer; ++j) {
+        const int i = lo + j;
+        if (i >= k) break;
+        if (i == 0 || keys[i] != keys[i - 1]) {
+            ++rank;
+            if (rank < d.kv) {
+                uniq[rank] = keys[i];
+                rep[rank] = vals[i];
+            }
+        }
+        key[vals[i]] = min(rank, d.kv - 1);   // ids stay inside planned tables
+        if (i == k - 1) {
+            if (rank + 1 != d.kv) atomicExch(err, 1 + node);
+            for (int r = rank + 1; r < d.kv; ++r) {   // count mismatch: keep tables valid
+                uniq[r] = 0;
+                rep[r] = 0;
+            }
+        }
+    }
+}
+
+size_t trie_sort_scratch_bytes(int k) {
+    const size_t nb = size_t((k + kRsTile - 1) / kRsTile);
+    return 2 * size_t(k) * 8 + 2 * size_t(k) * 4 + 256 * nb * 4 + nb * 4 + 4 * 256;
+}
+
+cudaError_t launch_trie_keys_large(const TrieDesc* d_desc, const TrieDesc* h_desc, int n_nodes,
+                                   const uint64_t* bits, int k, const int32_t* pi, char* tables, char* scratch,
+                                   int32_t* err, cudaStream_t st) {
+    const int nb = (k + kRsTile - 1) / kRsTile;
+    uint64_t* k0 = reinterpret_cast<uint64_t*>(scratch);
+    uint64_t* k1 = k0 + k;
+    int32_t* v0 = reinterpret_cast<int32_t*>(k1 + k);
+    int32_t* v1 = v0 + k;
+    int32_t* hist = v1 + k;
+    int32_t* cnt = hist + 256 * nb;
+    for (int node = 0; node < n_nodes; ++node) {
+        const int width = h_desc[node].b - h_desc[node].a;
+        k_rs_extract<<<grid_for(k, kRsThreads, 4096), kRsThreads, 0, st>>>(d_desc, node, bits, k, pi, k0, v0);
+        for (int shift = 0; shift < width; shift += 8) {
+            k_rs_hist<<<nb, kRsThreads, 0, st>>>(k0, k, shift, hist, nb);
+            k_rs_scan<<<1, 1024, 0, st>>>(hist, 256 * nb);
+            k_rs_scatter<<<nb, kRsThreads, 0, st>>>(k0, v0, k1, v1, k, shift, hist, nb);
+            std::swap(k0, k1);
+            std::swap(v0, v1);
+        }
+        k_rs_flags<<<nb, kRsThreads, 0, st>>>(k0, k, cnt);
+        k_rs_scan<<<1, 1024, 0, st>>>(cnt, nb);
+        k_rs_rank<<<nb, kRsThreads, 0, st>>>(d_desc, node, k0, v0, k, cnt, tables, err);
+    }
     return cudaGetLastError();
 }
 

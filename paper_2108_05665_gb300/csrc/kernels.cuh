@@ -8,6 +8,7 @@
 namespace xebk {
 
 constexpr int kMaxTrieK = 16384;  // bitstrings per single-CTA key-table sort
+constexpr int kMaxK = 1 << 24;     // bitstrings per plan (multi-CTA key-table sort beyond kMaxTrieK)
 
 // Memo key table of one tree node that depends on output bits (a1).
 struct TrieDesc {
@@ -125,6 +126,12 @@ size_t tc_wimg_floats(const TcDesc& t);
 cudaError_t prepare_kernels();
 cudaError_t launch_trie_keys(const TrieDesc* d_desc, int n_nodes, const uint64_t* bits, int k,
                              const int32_t* pi, char* tables, int32_t* err, cudaStream_t st);
+// a1 for k > kMaxTrieK: scratch of trie_sort_scratch_bytes(k) bytes (256-byte
+// aligned); h_desc = host copy of the node descriptors
+size_t trie_sort_scratch_bytes(int k);
+cudaError_t launch_trie_keys_large(const TrieDesc* d_desc, const TrieDesc* h_desc, int n_nodes,
+                                   const uint64_t* bits, int k, const int32_t* pi, char* tables, char* scratch,
+                                   int32_t* err, cudaStream_t st);
 cudaError_t launch_trie_links(const TrieDesc* d_desc, const int* d_internal, int n_internal,
                               int max_kv, char* tables, cudaStream_t st);
 template <typename T>
