@@ -347,7 +347,9 @@ def main():
                      if traffic is not None else "no capture of the current kernel source",
                      "per_launch_ms": per_launch_ms,
                      "share_of_step": d["ms"] / ms_total},
-        "kernels": {kname: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+        "kernels": {kname: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                            "alg_gbps": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None,
+                            "alg_tflops": v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else None}
                     for kname, v in prof.items()},
         "clocks": clocks,
     }

@@ -227,6 +227,7 @@ enum {
     XEB_KC_XEB = 8,           /* a7 gather + linear XEB                          */
     XEB_KC_GEMM_TC = 9,       /* a4 tcgen05 split-precision complex GEMM         */
     XEB_KC_GEMM_STREAM = 10,  /* a4 memory-bound streaming contraction (SIMT)    */
+    XEB_KC_GEMM_MEMO = 11,    /* a4 memo-trie levels: keys grouped by left key   */
     XEB_N_KC = 16
 };
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -243,7 +244,8 @@ struct xeb_plan_s {
     size_t bytes_total = 0;
     // offsets inside tables (bytes)
     int64_t t_trie_desc = 0, t_internal = 0, t_leaf_desc = 0, t_pi = 0, t_bits = 0, t_acc = 0, t_amps = 0,
-            t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0, t_sort = 0;
+            t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0, t_sort = 0, t_memo = 0;
+    size_t memo_bytes = 0;
     int n_sms = 152;
     int64_t tables_bytes = 0;
     std::vector<xebk::TrieDesc> trie;
@@ -510,34 +512,47 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         }
         if (!have) return fail(XEB_EINVAL, "planner found no valid tree: " + err);
     }
-    // slicing (App. A, "Slicing"): add the leg with the best memory reduction
-    // until the arena fits the budget
+    // slicing (App. A, "Slicing"): while the arena exceeds the budget, add the
+    // leg that minimises the objective f (memory penalty + log2 of the total
+    // time over all slices), so a leg that shrinks memory without multiplying
+    // the work is preferred; ties go to the smaller arena, then the smaller
+    // largest tensor, then the smaller total tensor size.
     if (!slices) {
+        auto node_elems = [](const Analysis& an, int v) {
+            return double(an.nodes[v].kv) * std::ldexp(1.0, int(an.nodes[v].legs.size()));
+        };
+        auto measure = [&](const Candidate& c) {
+            double mx = 0, tot = 0;
+            for (size_t v = 0; v < c.an.nodes.size(); ++v) {
+                const double e = node_elems(c.an, int(v));
+                mx = std::max(mx, e);
+                tot += e;
+            }
+            return std::array<double, 4>{c.f, double(c.arena_bytes), mx, tot};
+        };
         while (uint64_t(best.arena_bytes) > o.mem_budget && p->sliced.size() < 30) {
-            std::vector<int> order(best.an.nodes.size());
-            for (size_t v = 0; v < order.size(); ++v) order[v] = int(v);
-            std::sort(order.begin(), order.end(), [&](int x, int y) {
-                const double ex = double(best.an.nodes[x].kv) * std::ldexp(1.0, int(best.an.nodes[x].legs.size()));
-                const double ey = double(best.an.nodes[y].kv) * std::ldexp(1.0, int(best.an.nodes[y].legs.size()));
-                return ex > ey;
-            });
+            const auto mb = measure(best);
             std::vector<int> legs;
-            for (int t = 0; t < std::min<int>(3, int(order.size())); ++t)
-                for (int l : best.an.nodes[order[t]].legs)
-                    if (std::find(legs.begin(), legs.end(), l) == legs.end()) legs.push_back(l);
+            for (size_t v = 0; v < best.an.nodes.size(); ++v)
+                if (node_elems(best.an, int(v)) * 2 >= mb[2])
+                    for (int l : best.an.nodes[v].legs)
+                        if (std::find(legs.begin(), legs.end(), l) == legs.end()) legs.push_back(l);
             Candidate bc;
+            std::array<double, 4> bm{};
             int bl = -1;
             for (int l : legs) {
                 std::vector<int> s2 = p->sliced;
                 s2.push_back(l);
                 Candidate c;
                 if (!evaluate(p->net, best.tree, s2, dc, o, p->elem, k, c, err)) continue;
-                if (bl < 0 || c.arena_bytes < bc.arena_bytes) {
+                const auto m = measure(c);
+                if (bl < 0 || m < bm) {
                     bc = std::move(c);
+                    bm = m;
                     bl = l;
                 }
             }
-            if (bl < 0 || bc.arena_bytes >= best.arena_bytes) break;
+            if (bl < 0 || !(bm < mb)) break;
             p->sliced.push_back(bl);
             best = std::move(bc);
         }
@@ -700,6 +715,15 @@ void layout_device(xeb_plan_s* p) {
     p->t_err = take(16);
     p->t_wimg = take(p->opts.precision == XEB_PREC_TF32X3 ? 2 * 4 * 128 * 32 * 4 : 16);
     p->t_sort = take(p->k > size_t(xebk::kMaxTrieK) ? int64_t(xebk::trie_sort_scratch_bytes(int(p->k))) : 16);
+    {   // memo-level contractions: per-group A offsets + packed B vectors (largest op)
+        size_t mx = 16;
+        for (const Op& op : p->prog.ops)
+            if (op.kind != OP_PERM && op.N == 1 && op.kv > 1)
+                mx = std::max(mx, xebk::memo_scratch_bytes(std::max(an.nodes[op.a_node].kv, an.nodes[op.b_node].kv),
+                                                           op.kv, op.K, p->elem));
+        p->t_memo = take(int64_t(mx));
+        p->memo_bytes = mx;
+    }
     p->tables_bytes = t;
     p->bytes_total = size_t(off + t);
 }
@@ -850,7 +874,8 @@ void build_launches(xeb_plan_s* p) {
                 if (g.tc.tma && (p->opts.reserved[3] == 1 ||
                                  !encode_a_map(g.tc, reinterpret_cast<const float2*>(p->ws + p->off_arena), g.tmap)))
                     g.tc.tma = 0;
-            } else if (stream_tile(op, p->elem, g.s)) g.kernel = xebk::GK_STREAM;
+            } else if (stream_tile(op, p->elem, g.s))
+                g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
             else if (op.N == 1) g.kernel = xebk::GK_GEMV;
             else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;
             else g.kernel = xebk::GK_GENERIC;
@@ -980,7 +1005,12 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 }
             }
         }
-        if (p->gemms[i].kernel == xebk::GK_STREAM) {
+        if (p->gemms[i].kernel == xebk::GK_MEMO &&
+            xebk::memo_scratch_bytes(p->gemms[i].d.n_groups, g.kv, g.K, p->elem) > p->memo_bytes) {
+            why = "memo-level scratch of node " + std::to_string(op.node);
+            return false;
+        }
+        if (p->gemms[i].kernel == xebk::GK_STREAM || p->gemms[i].kernel == xebk::GK_MEMO) {
             const xebk::StreamDesc& sd = p->gemms[i].s;
             if (sd.T > 32 || sd.T != sd.tm + g.nak || (1 << sd.tm) != sd.R || sd.R > g.M || sd.R < 1) {
                 why = "stream tile of node " + std::to_string(op.node);
@@ -1031,8 +1061,8 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
                 const double by = es * (ka * double(op.M * op.K) + kb * double(op.K * op.N) +
                                         double(op.kv) * double(op.M * op.N));
-                static const int cls_of[5] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
-                                              XEB_KC_GEMM_TAIL, XEB_KC_GEMM_STREAM};
+                static const int cls_of[6] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
+                                              XEB_KC_GEMM_TAIL, XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO};
                 ProfScope ps(p, st, g.kernel >= GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by);
                 if (g.kernel == GK_TC) {
                     if constexpr (sizeof(T) == 8)
@@ -1040,6 +1070,8 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 } else if (g.kernel == GK_TC2) {
                     if constexpr (sizeof(T) == 8)
                         XEB_CUDA(xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st));
+                } else if (g.kernel == xebk::GK_MEMO) {
+                    XEB_CUDA(xebk::launch_gemm_memo<T>(g.d, g.s, arena, tables + p->t_memo, st));
                 } else if (g.kernel == xebk::GK_STREAM) {
                     XEB_CUDA(xebk::launch_gemm_stream<T>(g.d, g.s, arena, st));
                 } else {

@@ -767,11 +767,32 @@ __global__ void __launch_bounds__(256, 2) k_gemm_stream(const __grid_constant__ 
                 }
                 __syncthreads();
                 const int rows = rows_left < R ? int(rows_left) : R;
-                for (int pr = tid; pr < rows * nb; pr += 256) {
-                    const int r = pr % rows, j = pr / rows;
-                    T acc = czero<T>();
-                    for (int k = 0; k < K; ++k) acc = cfma(acc, cur[k * ldA + r], Bs[j * K + k]);
-                    arena[g.c_off + (ub0 + j) * g.c_key + mt * R + r] = acc;
+                if (K <= 16) {
+                    // a thread keeps its row of A in registers and walks its
+                    // share of the keys; a warp covers 32 consecutive rows of
+                    // one key, so B is read as a broadcast and C stores coalesce
+                    const int S = R >= 256 ? 1 : 256 / R;   // threads per row
+                    const int rs = R >= 256 ? 256 : R;       // row stride
+                    for (int r = R >= 256 ? tid : tid % R; r < rows; r += rs) {
+                        T a[16];
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) a[k] = k < K ? cur[k * ldA + r] : czero<T>();
+                        for (int j = R >= 256 ? 0 : tid / R; j < nb; j += S) {
+                            const T* b = Bs + j * K;
+                            T acc = czero<T>();
+#pragma unroll
+                            for (int k = 0; k < 16; ++k)
+                                if (k < K) acc = cfma(acc, a[k], b[k]);
+                            arena[g.c_off + (ub0 + j) * g.c_key + mt * R + r] = acc;
+                        }
+                    }
+                } else {
+                    for (int pr = tid; pr < rows * nb; pr += 256) {
+                        const int r = pr % rows, j = pr / rows;
+                        T acc = czero<T>();
+                        for (int k = 0; k < K; ++k) acc = cfma(acc, cur[k * ldA + r], Bs[j * K + k]);
+                        arena[g.c_off + (ub0 + j) * g.c_key + mt * R + r] = acc;
+                    }
                 }
                 __syncthreads();
             }
@@ -802,6 +823,185 @@ __global__ void __launch_bounds__(256, 2) k_gemm_stream(const __grid_constant__ 
         __syncthreads();
     }
     cp_async_wait<0>();
+}
+
+// ---- memo-trie levels: many keys per A tile, N = 1 ---------------------------------
+// C_u[m] = sum_k A_{uL(u)}[m][k] B_{uR(u)}[k] for the keys u of each left-key
+// group.  A prep kernel writes every group's A offset and packs every key's B
+// vector contiguously (keys are ordered by uL then uR, so a group's vectors
+// are one run); the main loop then loads a tile's A rows and its group's B
+// vectors together with cp.async, kStreamStages - 1 tiles ahead, and reads
+// the next tile's group data one iteration before it issues those loads, so
+// no dependent global read sits on the critical path.
+template <typename T>
+__global__ void k_memo_prep(const __grid_constant__ GemmDesc g, const T* __restrict__ arena, int64_t* grp_a,
+                            T* bpack) {
+    const int64_t K = g.K;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < g.n_groups; i += stride)
+        grp_a[i] = int64_t(g.uL[g.gstart[i]]) * g.a_key;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < g.kv * K; e += stride) {
+        const int64_t u = e / K, k = e % K;
+        bpack[e] = arena[g.b_off + int64_t(g.uR[u]) * g.b_key + scatter(k, g.bpk, g.nbk)];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_gemm_memo(const __grid_constant__ GemmDesc g,
+                                                      const __grid_constant__ StreamDesc s, T* __restrict__ arena,
+                                                      const int64_t* __restrict__ grp_a,
+                                                      const T* __restrict__ bpack) {
+    extern __shared__ __align__(16) unsigned char sm_memo[];
+    const int R = s.R, K = int(g.K);
+    const int ldA = R + 1;
+    const int a_sz = (K * ldA + 1) & ~1;
+    T* abuf = reinterpret_cast<T*>(sm_memo);                 // kStreamStages x [K][R+1]
+    T* bbuf = abuf + kStreamStages * a_sz;                     // kStreamStages x kMemoBPre
+    T* Bs = bbuf + kStreamStages * kMemoBPre;                  // synchronous staging (large groups)
+    int64_t* rowoff = reinterpret_cast<int64_t*>(Bs + kStreamBKeys);  // per row bit above the tile
+    int64_t* meta = rowoff + kMaxLegs;                         // per stage: u0, u1
+    const int tid = threadIdx.x;
+    for (int i = tid; i < g.nam; i += 256) rowoff[i] = int64_t(1) << g.apm[i];
+    const int tile_elems = R * K;
+    int32_t off[kStreamEPT];
+    int slot[kStreamEPT];
+#pragma unroll
+    for (int j = 0; j < kStreamEPT; ++j) {
+        const int e = tid + j * 256;
+        off[j] = 0;
+        slot[j] = -1;
+        if (e < tile_elems) {
+            int r = 0, k = 0, ri = 0, ki = 0;
+            int32_t o = 0;
+            for (int i = 0; i < s.T; ++i) {
+                const int bit = (e >> i) & 1;
+                if ((s.is_k >> i) & 1) k |= bit << ki++;
+                else r |= bit << ri++;
+                if (bit) o |= int32_t(1) << s.pos[i];
+            }
+            off[j] = o;
+            slot[j] = k * ldA + r;
+        }
+    }
+    __syncthreads();
+    const int64_t tpg = (g.M + R - 1) / R;   // tiles per group
+    const int64_t n_tiles = g.n_groups * tpg;
+    struct Meta {
+        int64_t u0, u1, aoff;
+    };
+    auto load_meta = [&](int64_t tile) {
+        Meta m{0, 0, 0};
+        if (tile < n_tiles) {
+            const int64_t grp = tile / tpg;
+            m.u0 = g.gstart[grp];
+            m.u1 = g.gstart[grp + 1];
+            m.aoff = grp_a[grp];
+        }
+        return m;
+    };
+    auto issue = [&](int64_t tile, int stage, const Meta& m) {
+        const int64_t mt = tile % tpg;
+        int64_t ro = 0;
+        for (int64_t x = (mt * R) >> s.tm, i = s.tm; x != 0; x >>= 1, ++i)
+            if (x & 1) ro += rowoff[i];
+        const T* A = arena + g.a_off + m.aoff + ro;
+        const int64_t rows_left = g.M - mt * R;
+        T* buf = abuf + stage * a_sz;
+#pragma unroll
+        for (int j = 0; j < kStreamEPT; ++j) {
+            if (slot[j] < 0) continue;
+            if (rows_left >= R || (slot[j] % ldA) < rows_left) cp_async_el(buf + slot[j], A + off[j]);
+            else buf[slot[j]] = czero<T>();
+        }
+        const int64_t nbk = (m.u1 - m.u0) * K;
+        if (nbk <= kMemoBPre) {
+            T* bb = bbuf + stage * kMemoBPre;
+            for (int64_t e = tid; e < nbk; e += 256) cp_async_el(bb + e, bpack + m.u0 * K + e);
+        }
+        if (tid == 0) {
+            meta[2 * stage] = m.u0;
+            meta[2 * stage + 1] = m.u1;
+        }
+    };
+    const int64_t G = gridDim.x;
+#pragma unroll
+    for (int p = 0; p < kStreamStages - 1; ++p) {
+        const int64_t tl = blockIdx.x + int64_t(p) * G;
+        if (tl < n_tiles) issue(tl, p, load_meta(tl));
+        cp_async_commit();
+    }
+    Meta next = load_meta(blockIdx.x + int64_t(kStreamStages - 1) * G);
+    int64_t tile = blockIdx.x;
+    for (int it = 0; tile < n_tiles; tile += G, ++it) {
+        const int stage = it % kStreamStages;
+        const int64_t ahead = tile + int64_t(kStreamStages - 1) * G;
+        const Meta m = next;
+        next = load_meta(ahead + G);   // used by the next iteration
+        if (ahead < n_tiles) issue(ahead, (it + kStreamStages - 1) % kStreamStages, m);
+        cp_async_commit();
+        cp_async_wait<kStreamStages - 1>();
+        __syncthreads();
+        const T* cur = abuf + stage * a_sz;
+        const int64_t u0 = meta[2 * stage], u1 = meta[2 * stage + 1];
+        const int64_t mt = tile % tpg;
+        const int64_t rows_left = g.M - mt * R;
+        const int rows = rows_left < R ? int(rows_left) : R;
+        const int64_t nkeys = u1 - u0;
+        const bool pre = nkeys * K <= kMemoBPre;
+        const int kb_max = pre ? int(nkeys) : kStreamBKeys / K;
+        for (int64_t ub0 = u0; ub0 < u1; ub0 += kb_max) {
+            const int nb = u1 - ub0 < kb_max ? int(u1 - ub0) : kb_max;
+            const T* Bv = bbuf + stage * kMemoBPre;
+            if (!pre) {
+                for (int e = tid; e < nb * K; e += 256) Bs[e] = bpack[ub0 * K + e];
+                __syncthreads();
+                Bv = Bs;
+            }
+            if (K <= 16) {
+                const int S = R >= 256 ? 1 : 256 / R;   // threads per row
+                const int rs = R >= 256 ? 256 : R;
+                for (int r = R >= 256 ? tid : tid % R; r < rows; r += rs) {
+                    T a[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) a[k] = k < K ? cur[k * ldA + r] : czero<T>();
+                    for (int j = R >= 256 ? 0 : tid / R; j < nb; j += S) {
+                        const T* b = Bv + j * K;
+                        T acc = czero<T>();
+#pragma unroll
+                        for (int k = 0; k < 16; ++k)
+                            if (k < K) acc = cfma(acc, a[k], b[k]);
+                        arena[g.c_off + (ub0 + j) * g.c_key + mt * R + r] = acc;
+                    }
+                }
+            } else {
+                for (int pr = tid; pr < rows * nb; pr += 256) {
+                    const int r = pr % rows, j = pr / rows;
+                    T acc = czero<T>();
+                    for (int k = 0; k < K; ++k) acc = cfma(acc, cur[k * ldA + r], Bv[j * K + k]);
+                    arena[g.c_off + (ub0 + j) * g.c_key + mt * R + r] = acc;
+                }
+            }
+            if (!pre) __syncthreads();
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+size_t memo_scratch_bytes(int64_t n_groups, int64_t kv, int64_t K, size_t elem) {
+    return size_t(n_groups) * 8 + 256 + size_t(kv * K) * elem;
+}
+
+template <typename T>
+cudaError_t launch_gemm_memo(const GemmDesc& g, const StreamDesc& s, T* arena, char* scratch, cudaStream_t st) {
+    int64_t* grp_a = reinterpret_cast<int64_t*>(scratch);
+    T* bpack = reinterpret_cast<T*>(scratch + ((size_t(g.n_groups) * 8 + 255) & ~size_t(255)));
+    k_memo_prep<T><<<grid_for(g.kv * g.K, 256, 152 * 8), 256, 0, st>>>(g, arena, grp_a, bpack);
+    const size_t a_sz = (size_t(g.K) * (s.R + 1) + 1) & ~size_t(1);
+    const size_t smem = sizeof(T) * (kStreamStages * (a_sz + kMemoBPre) + kStreamBKeys) + 8 * (kMaxLegs + 2 * kStreamStages);
+    const int64_t tiles = g.n_groups * ((g.M + s.R - 1) / s.R);
+    k_gemm_memo<T><<<grid_for(tiles, 1, 152 * 8), 256, smem, st>>>(g, s, arena, grp_a, bpack);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -928,6 +1128,10 @@ cudaError_t prepare_kernels() {
     XEB_PREP_STREAM(double2, 1) XEB_PREP_STREAM(double2, 2) XEB_PREP_STREAM(double2, 4)
     XEB_PREP_STREAM(double2, 8) XEB_PREP_STREAM(double2, 16)
 #undef XEB_PREP_STREAM
+    e = cudaFuncSetAttribute(k_gemm_memo<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gemm_memo<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    if (e != cudaSuccess) return e;
     e = prepare_tc_kernels();
     if (e != cudaSuccess) return e;
     done = true;
@@ -943,6 +1147,8 @@ template cudaError_t launch_gemm<float2>(int, const GemmDesc&, float2*, cudaStre
 template cudaError_t launch_gemm<double2>(int, const GemmDesc&, double2*, cudaStream_t);
 template cudaError_t launch_gemm_stream<float2>(const GemmDesc&, const StreamDesc&, float2*, cudaStream_t);
 template cudaError_t launch_gemm_stream<double2>(const GemmDesc&, const StreamDesc&, double2*, cudaStream_t);
+template cudaError_t launch_gemm_memo<float2>(const GemmDesc&, const StreamDesc&, float2*, char*, cudaStream_t);
+template cudaError_t launch_gemm_memo<double2>(const GemmDesc&, const StreamDesc&, double2*, char*, cudaStream_t);
 template cudaError_t launch_root_accum<float2>(const float2*, double2*, int64_t, cudaStream_t);
 template cudaError_t launch_root_accum<double2>(const double2*, double2*, int64_t, cudaStream_t);
 

@@ -80,11 +80,12 @@ struct StreamDesc {
     int8_t pos[32];
 };
 
-enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4 };
+enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4, GK_MEMO = 5 };
 constexpr int kStreamMaxK = 64, kStreamMaxN = 64;
 constexpr int kStreamEPT = 8;   // A-tile elements per thread
 constexpr int kStreamStages = 4;  // A tiles in flight per CTA
 constexpr int kStreamBKeys = 2048;  // B elements staged per key batch (N == 1)
+constexpr int kMemoBPre = 512;      // memo levels: B elements loaded with each tile (one left-key group)
 
 // tcgen05 split-precision contraction (one key, M % 128 == 0, 16 <= K, N <= 64).
 // Tile bits of one K-chunk: the 7 lowest row bits and the 4 lowest summed
@@ -143,6 +144,11 @@ template <typename T>
 cudaError_t launch_gemm(int kernel, const GemmDesc& g, T* arena, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena, cudaStream_t st);
+// memo-trie levels (N = 1, keys grouped by uL): scratch of memo_scratch_bytes
+// for the per-group A offsets and the packed B vectors
+size_t memo_scratch_bytes(int64_t n_groups, int64_t kv, int64_t K, size_t elem);
+template <typename T>
+cudaError_t launch_gemm_memo(const GemmDesc& g, const StreamDesc& s, T* arena, char* scratch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);
