@@ -119,6 +119,9 @@ typedef struct {
                              replaying one captured CUDA graph per step;
                              [3] = 1: tensor-core contractions gather A with
                              plain loads even where TMA boxes could load it;
+                             [4] = 1: memo-trie levels with long groups run as
+                             grouped tensor-core GEMMs (default: the SIMT
+                             memo-level kernel, faster for K = 16 tiles);
                              others 0 */
 } xeb_plan_opts;
 

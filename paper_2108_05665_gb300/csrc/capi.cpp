@@ -150,6 +150,45 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits, bool tmem_variant) {
     return true;
 }
 
+// Grouped tensor-core form of a memo-level contraction (N = 1, keys grouped
+// by their left key): each group is a GEMM whose columns are the group's keys,
+// their B vectors packed contiguously by the memo prep kernel.  Possible when
+// groups are long (>= 512 tiles) and hold at most 64 keys; opt-in, because
+// with K = 16 a tile is one 32 KB chunk and the kernel's per-tile hand-offs
+// cost more than the SIMT memo-level kernel's arithmetic.
+bool tc_grouped(const Analysis& an, const Op& op, const xebk::GemmDesc& d, xebk::TcDesc& t) {
+    if (op.N != 1 || op.kv <= 1 || !d.gstart || !d.c_natural) return false;
+    if (op.M < (int64_t(1) << 16) || op.K < 16 || op.K > 64) return false;
+    const int64_t kvB = an.nodes[op.b_node].kv;
+    if (kvB > 64 || d.c_key != op.M) return false;
+    int64_t npad = 16;
+    while (npad < kvB) npad *= 2;
+    int lk = 0, ln = 0, lm = 0;
+    while ((int64_t(1) << lk) < op.K) ++lk;
+    while ((int64_t(1) << ln) < npad) ++ln;
+    while ((int64_t(1) << lm) < op.M) ++lm;
+    Op o2 = op;
+    o2.kv = 1;
+    o2.N = npad;
+    o2.b_pos_k.clear();
+    o2.b_pos_n.clear();
+    o2.c_pos_m.clear();
+    o2.c_pos_n.clear();
+    for (int i = 0; i < lk; ++i) o2.b_pos_k.push_back(i);
+    for (int i = 0; i < ln; ++i) o2.b_pos_n.push_back(lk + i);
+    for (int i = 0; i < lm; ++i) o2.c_pos_m.push_back(i);
+    for (int i = 0; i < ln; ++i) o2.c_pos_n.push_back(lm + i);
+    o2.c_hint.clear();
+    if (!tc_tile(o2, t, xebk::kTc2RowBits, true)) return false;
+    t.tma = 0;
+    t.grp = 1;
+    t.tpg = op.M >> xebk::kTc2RowBits;
+    t.n_groups = d.n_groups;
+    t.c_key = d.c_key;
+    t.gstart = d.gstart;
+    return true;
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -874,6 +913,18 @@ void build_launches(xeb_plan_s* p) {
                 if (g.tc.tma && (p->opts.reserved[3] == 1 ||
                                  !encode_a_map(g.tc, reinterpret_cast<const float2*>(p->ws + p->off_arena), g.tmap)))
                     g.tc.tma = 0;
+            } else if (p->opts.precision == XEB_PREC_TF32X3 && p->opts.reserved[1] != 1 &&
+                       p->opts.reserved[4] == 1 && tc_grouped(p->an, op, d, g.tc)) {
+                g.kernel = GK_TC2;
+                g.tc.a_off = d.a_off;
+                g.tc.b_off = 0;
+                g.tc.c_off = d.c_off;
+                g.tc.wimg = reinterpret_cast<float*>(tables + p->t_wimg);
+                g.tc.err = reinterpret_cast<int32_t*>(tables + p->t_err);
+                g.tc.grp_a = reinterpret_cast<const int64_t*>(tables + p->t_memo);
+                g.tc.bpack_off = (p->off_tables + p->t_memo + ((d.n_groups * 8 + 255) & ~int64_t(255))) / 8;
+                std::memset(&g.tmap, 0, sizeof(g.tmap));
+                g.s = xebk::StreamDesc{};
             } else if (stream_tile(op, p->elem, g.s))
                 g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
             else if (op.N == 1) g.kernel = xebk::GK_GEMV;
@@ -948,11 +999,24 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
         if (p->gemms[i].kernel == GK_TC || p->gemms[i].kernel == GK_TC2) {
             const xebk::TcDesc& t = p->gemms[i].tc;
             const int row_bits = p->gemms[i].kernel == GK_TC2 ? xebk::kTc2RowBits : 7;
-            if (t.M != g.M || t.M % (int64_t(1) << row_bits) != 0 || t.K2 != 2 * g.K || t.N2 != 2 * g.N ||
+            // grouped memo-level form: the columns are a group's keys (N2/2 of them at most)
+            const bool grp = p->gemms[i].kernel == GK_TC2 && t.grp;
+            int lnp = 0;
+            while ((2 << lnp) < t.N2) ++lnp;
+            const int64_t gN = grp ? t.N2 / 2 : g.N;
+            const int nbn_eff = grp ? lnp : g.nbn;
+            if (t.M != g.M || t.M % (int64_t(1) << row_bits) != 0 || t.K2 != 2 * g.K || t.N2 != 2 * gN ||
                 t.K2 % 32 != 0 || t.N2 % 32 != 0 || t.N2 > 128 || t.K2 > 128 || t.n_chunks * 32 != t.K2 ||
-                t.n_chunks > 4 || t.T != row_bits + 4 || g.kv != 1 ||
+                t.n_chunks > 4 || t.T != row_bits + 4 || (!grp && g.kv != 1) ||
                 xebk::tc_wimg_floats(t) * 4 > size_t(2 * 4 * 128 * 32 * 4)) {
                 why = "tensor-core tile of node " + std::to_string(op.node);
+                return false;
+            }
+            if (grp && (t.tma || (t.tpg << row_bits) != g.M || t.n_groups != g.n_groups || t.c_key != g.M ||
+                        t.N2 / 2 < an.nodes[op.b_node].kv || t.n_groups != an.nodes[op.a_node].kv ||
+                        xebk::memo_scratch_bytes(t.n_groups, g.kv, g.K, 8) > p->memo_bytes ||
+                        !inside(op.c_buf, t.c_off, t.c_off + g.kv * t.c_key - 1))) {
+                why = "grouped tensor-core form of node " + std::to_string(op.node);
                 return false;
             }
             // largest element a loader can touch
@@ -962,15 +1026,15 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             int64_t rowhi = 0;
             for (int i = row_bits; i < t.nam; ++i) rowhi |= int64_t(1) << t.apm[i];
             if ((p->gemms[i].kernel == GK_TC && !inside(op.a_buf, t.a_off, t.a_off + rowhi + hi)) ||
-                !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1)) {
+                (!grp && !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1))) {
                 why = "tensor-core operand of node " + std::to_string(op.node);
                 return false;
             }
             for (int i = 0; i < t.T; ++i)
                 if (t.pos[i] < 0 || t.pos[i] >= op.a_rank) { why = "tensor-core tile positions"; return false; }
             if (p->gemms[i].kernel == GK_TC2) {
-                const int rc = g.nam + g.nbn;
-                if (t.n_ext + row_bits != g.nam || t.n_ext > 32 || t.Tst != row_bits + g.nbn || t.Tst < row_bits + 4 ||
+                const int rc = g.nam + nbn_eff;
+                if (t.n_ext + row_bits != g.nam || t.n_ext > 32 || t.Tst != row_bits + nbn_eff || t.Tst < row_bits + 4 ||
                     t.Tst > 16) {
                     why = "tensor-core result tile of node " + std::to_string(op.node);
                     return false;
@@ -984,7 +1048,8 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 for (int i2 = 0; i2 < t.n_ext; ++i2) ahi |= int64_t(1) << t.ext_apos[i2];
                 int64_t thi = 0;
                 for (int i2 = 0; i2 < t.T; ++i2) thi |= int64_t(1) << t.pos[i2];
-                if (!inside(op.a_buf, t.a_off, t.a_off + ahi + thi + t.chunk_off[t.n_chunks - 1])) {
+                const int64_t akey = grp ? (an.nodes[op.a_node].kv - 1) * g.a_key : 0;   // largest group A offset
+                if (!inside(op.a_buf, t.a_off, t.a_off + akey + ahi + thi + t.chunk_off[t.n_chunks - 1])) {
                     why = "tensor-core operand rows of node " + std::to_string(op.node);
                     return false;
                 }
@@ -1068,8 +1133,12 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                     if constexpr (sizeof(T) == 8)
                         XEB_CUDA(xebk::launch_tc_gemm(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st));
                 } else if (g.kernel == GK_TC2) {
-                    if constexpr (sizeof(T) == 8)
+                    if constexpr (sizeof(T) == 8) {
+                        if (g.tc.grp)
+                            XEB_CUDA(xebk::launch_memo_prep<float2>(g.d, reinterpret_cast<float2*>(arena),
+                                                                    tables + p->t_memo, st));
                         XEB_CUDA(xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st));
+                    }
                 } else if (g.kernel == xebk::GK_MEMO) {
                     XEB_CUDA(xebk::launch_gemm_memo<T>(g.d, g.s, arena, tables + p->t_memo, st));
                 } else if (g.kernel == xebk::GK_STREAM) {

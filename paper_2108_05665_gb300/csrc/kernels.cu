@@ -988,6 +988,15 @@ __global__ void __launch_bounds__(256, 2) k_gemm_memo(const __grid_constant__ Ge
     cp_async_wait<0>();
 }
 
+template <typename T>
+cudaError_t launch_memo_prep(const GemmDesc& g, T* arena, char* scratch, cudaStream_t st) {
+    int64_t* grp_a = reinterpret_cast<int64_t*>(scratch);
+    T* bpack = reinterpret_cast<T*>(scratch + ((size_t(g.n_groups) * 8 + 255) & ~size_t(255)));
+    k_memo_prep<T><<<grid_for(g.kv * g.K, 256, 152 * 8), 256, 0, st>>>(g, arena, grp_a, bpack);
+    return cudaGetLastError();
+}
+template cudaError_t launch_memo_prep<float2>(const GemmDesc&, float2*, char*, cudaStream_t);
+
 size_t memo_scratch_bytes(int64_t n_groups, int64_t kv, int64_t K, size_t elem) {
     return size_t(n_groups) * 8 + 256 + size_t(kv * K) * elem;
 }

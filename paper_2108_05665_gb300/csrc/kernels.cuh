@@ -116,6 +116,15 @@ struct TcDesc {
     // and an outside-tile A address bit p is row bit p - row_shift
     int tma, box_log2, row_shift;
     int32_t box_y[16];
+    // (tensor-memory variant, gather mode) grouped mode for memo-trie levels:
+    // tiles g * tpg .. (g + 1) * tpg - 1 belong to left-key group g, whose A
+    // starts grp_a[g] elements after a_off and whose keys gstart[g] ..
+    // gstart[g + 1] - 1 form the columns: key u's B vector (K complex) sits at
+    // bpack_off + u K and its results at c_off + u c_key + row
+    int grp;
+    int64_t tpg, n_groups, c_key, bpack_off;
+    const int32_t* gstart;
+    const int64_t* grp_a;
 };
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 constexpr int kTc2RowBits = 7;               // tensor-memory variant: 128 state rows per tile
@@ -149,6 +158,10 @@ cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena,
 size_t memo_scratch_bytes(int64_t n_groups, int64_t kv, int64_t K, size_t elem);
 template <typename T>
 cudaError_t launch_gemm_memo(const GemmDesc& g, const StreamDesc& s, T* arena, char* scratch, cudaStream_t st);
+// the memo-level prep alone (per-group A offsets, packed B vectors), for the
+// grouped tensor-core path
+template <typename T>
+cudaError_t launch_memo_prep(const GemmDesc& g, T* arena, char* scratch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStream_t st);
 cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* cst = reinterpret_cast<float*>(ring + kRing * kStageBytes);  // kRows x kCStride
     Sm2* S = reinterpret_cast<Sm2*>(cst + kRows * kCStride);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t n_tiles = t.M / kRows;
+    const int64_t n_tiles = t.grp ? t.n_groups * t.tpg : t.M / kRows;
     const int nch = t.n_chunks;
     if (tid == 0) {
         for (int s = 0; s < kRing; ++s) {
@@ -316,10 +316,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         // issue-side cursor (chunks are issued in order)
         int64_t ld_tile = blockIdx.x;
         int ld_c = 0;
+        int64_t cg = -1, cga = 0;   // grouped mode: last group seen and its A offset
         auto tile_base = [&](int64_t tile) {
             int64_t b = 0;
+            if (t.grp) {
+                const int64_t g = tile / t.tpg;
+                tile -= g * t.tpg;
+                if (g != cg) {
+                    cg = g;
+                    cga = t.grp_a[g];
+                }
+                b = cga;
+            }
             for (int i = 0; i < t.n_ext; ++i)
-                if ((tile >> i) & 1) b |= int64_t(1) << t.ext_apos[i];
+                if ((tile >> i) & 1) b += int64_t(1) << t.ext_apos[i];
             return b;
         };
         const float2* Arow = arena + t.a_off + tile_base(ld_tile) + t.chunk_off[0];
@@ -409,14 +419,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = widx >> 2;              // which share of columns / rows
         constexpr int kShares = kEpiWarps / 4;
         const int np = q * 32 + lane;            // W^T row = output column n' (0..127)
-        {
+        // W^T (big, small) of the columns of `tile` into tensor memory; in
+        // grouped mode the columns are the keys of the tile's group
+        auto write_wt = [&](int64_t tile) {
             const int n = np >> 1, cpart = np & 1;
-            const bool live = np < t.N2;
+            bool live = np < t.N2;
+            const float2* B = arena + t.b_off;
+            if (t.grp) {
+                const int64_t g = tile / t.tpg;
+                const int64_t u0 = t.gstart[g];
+                live = np < 2 * (t.gstart[g + 1] - u0);
+                B = arena + t.bpack_off + u0 * (t.K2 / 2);
+            }
             int64_t noff = 0;
             if (live)
                 for (int i = 0; i < t.nbn; ++i)
                     if ((n >> i) & 1) noff |= int64_t(1) << t.bpn[i];
-            const float2* B = arena + t.b_off;
             for (int c0 = 32 * half; c0 < t.K2; c0 += 32 * kShares) {
                 float vb[32], vs[32];
 #pragma unroll
@@ -438,9 +456,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tm_st32(w_small + lanes + uint32_t(c0), vs);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            fence_before();
-            bar_arrive(&S->wready);
-        }
+        };
+        if (blockIdx.x < n_tiles) write_wt(blockIdx.x);
+        fence_before();
+        bar_arrive(&S->wready);
         uint32_t tc = 0, ep = 0;
         const uint32_t lanes = uint32_t(q * 32) << 16;
         // Result tile element e (its bits in ascending C address order) =
@@ -498,6 +517,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool got = bar_wait(&S->tfull[b], ub & 1, t.err, 16);
             if (!__all_sync(0xffffffffu, got)) break;
             fence_after();
+            // grouped mode: the next tile of this CTA needs its group's W^T,
+            // written after this tile's accumulators are read and before they
+            // are released (the MMAs of this tile are complete by then)
+            const int64_t nxt = tile + gridDim.x;
+            const bool switch_w = t.grp && nxt < n_tiles && nxt / t.tpg != tile / t.tpg;
             // D^T: lane = output column np, column = tile row; tensor memory is
             // released for the next tile's MMAs once the last load has landed
             const uint32_t db = tmem + 256;
@@ -507,17 +531,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tm_ld32(db + lanes + uint32_t(r0), v);
                 tm_ld32(db + lanes + kRows + uint32_t(r0), w);
                 tm_wait_ld();
-                if (r0 == (half + 1) * kMyRows - 32) {
+                if (r0 == (half + 1) * kMyRows - 32 && !switch_w) {
                     fence_before();
                     bar_arrive(&S->tempty[b]);
                 }
 #pragma unroll
                 for (int i = 0; i < 32; ++i) cst[(r0 + i) * kCStride + np] = v[i] + w[i];
             }
+            if (switch_w) {
+                write_wt(nxt);
+                fence_before();
+                bar_arrive(&S->tempty[b]);
+            }
             if (!__all_sync(0xffffffffu, epi_sync())) break;
-            int64_t cbase = 0;
+            int64_t cbase = 0, mt = tile;
+            int nk = 1 << 30;   // grouped mode: keys (columns) of this tile's group
+            if (t.grp) {
+                const int64_t g = tile / t.tpg;
+                mt = tile - g * t.tpg;
+                const int64_t u0 = t.gstart[g];
+                nk = int(t.gstart[g + 1] - u0);
+                cbase = u0 * t.c_key;
+            }
             for (int i = 0; i < t.n_ext; ++i)
-                if ((tile >> i) & 1) cbase |= int64_t(1) << t.ext_cpos[i];
+                if ((mt >> i) & 1) cbase += int64_t(1) << t.ext_cpos[i];
             float2* C = arena + t.c_off + cbase;
             const float2* st2 = reinterpret_cast<const float2*>(cst);
             if (e_active) {
@@ -535,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (j < nlo) v[j] = st2[sm2 + s8[j]];
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (j < nlo) C[gm + g8[j]] = v[j];
+                        if (j < nlo && (sm2 + s8[j]) % (kCStride / 2) < nk) C[gm + g8[j]] = v[j];
                 }
             }
             if (!__all_sync(0xffffffffu, epi_sync())) break;

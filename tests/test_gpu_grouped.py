@@ -1,0 +1,48 @@
+"""Memo-trie levels as grouped tensor-core GEMMs (one GEMM per left-key group,
+its keys as the columns) against the FP64 oracle and against the SIMT
+memo-level kernel on the same plan."""
+import numpy as np
+import pytest
+
+from paper_2108_05665_gb300 import binding as B, build, inputs
+from oracle import statevec, xeb
+from gpu_util import rel_err, run
+
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = 1e-5
+TF32_F_TOL = 2e-5   # truncating tensor-core accumulation (see test_gpu_parity)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    build.build()
+    B.load()
+
+
+@pytest.fixture(scope="module")
+def grid4x6():
+    # the planner's tree for this circuit has a memo level of 16 groups x
+    # 16 keys with 65,536 rows each
+    circ = inputs.random_grid_circuit(4, 6, 12, 77)
+    bits = inputs.uniform_bitstrings(24, 2000, 78)
+    return circ, bits, statevec.amplitudes(circ, bits)
+
+
+def test_grouped_memo_levels(grid4x6):
+    circ, bits, ref = grid4x6
+    res = {}
+    for simt in (1, 0):
+        o = B.xeb_default_opts()
+        o.reserved[4] = 1 - simt   # 1: grouped tensor-core form
+        amps, F, plan = run(circ, bits, precision=B.XEB_PREC_TF32X3, opts=o)
+        st = plan.stats()
+        res[simt] = (amps, F, st["n_tc_launches"])
+        print("simt memo %d: tc launches %d, max rel err %.2e, F %.6f" %
+              (simt, st["n_tc_launches"], rel_err(amps, ref, 24).max(), F))
+        assert rel_err(amps, ref, 24).max() < AMP_TOL
+        assert abs(F - xeb.fidelity(ref, 24)) < TF32_F_TOL
+        plan.close()
+    assert res[0][2] == res[1][2] + 1   # the memo level ran as one grouped tensor-core launch
