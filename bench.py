@@ -210,6 +210,9 @@ def main():
                     help="launch the step kernel by kernel instead of replaying one captured CUDA graph")
     ap.add_argument("--tc-variant", default="tmem", choices=["tmem", "smem"],
                     help="tensor-core kernel: B^T in tensor memory (default) or split B in shared memory")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="time every kernel form of every contraction this many times and keep the fastest "
+                         "(plan-time, outside the timed region; 0 = off)")
     ap.add_argument("--tc-loads", default="tma", choices=["tma", "gather"],
                     help="tensor-core A operand: TMA boxes where A is row-major (default) or plain-load gathers")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
@@ -250,6 +253,11 @@ def main():
     k = len(bits)
     dev_bits = torch.from_numpy(bits.view(np.int64).copy()).cuda()
     out = torch.empty(2 * k, dtype=torch.float64, device="cuda")
+
+    tuned = None
+    if args.autotune > 0:
+        B.xeb_set_bitstrings(plan.handle, dev_bits.data_ptr(), k, sp)
+        tuned = B.xeb_plan_autotune(plan.handle, args.autotune, sp)
 
     def step():
         B.xeb_set_bitstrings(plan.handle, dev_bits.data_ptr(), k, sp)
@@ -329,6 +337,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": w.name, "desc": workload_desc(w), "precision": args.precision,
                    "tc_variant": args.tc_variant, "tc_loads": args.tc_loads,
+                   "autotune": ("%d reps per form, %d contractions changed form" % (args.autotune, tuned))
+                   if tuned is not None else "off",
                    "launch": "kernel by kernel" if args.eager else "one CUDA graph per step",
                    "planner": ["given", "greedy", "sweep"][st["planner_used"]], "n_slices": st["n_slices"],
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),

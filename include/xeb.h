@@ -261,6 +261,15 @@ xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* la
  * device address (with the device current); make that first call before any
  * stream capture.  All calls share the array, so calls whose kernels overlap
  * on the GPU race. */
+/* Autotuner (the plan's own form of "tile shapes picked by an autotuner"):
+ * runs one step to fill the operands, then for every contraction times each
+ * kernel form that fits it -- tcgen05 with TMA loads, tcgen05 with gathered
+ * loads, tcgen05 with W in shared memory, grouped tcgen05 (memo levels), SIMT
+ * streaming -- `reps` times with CUDA events on `stream`, and keeps the
+ * fastest.  Later steps use (and recapture) the chosen forms.  Synchronises
+ * `stream`.  n_changed (may be NULL): contractions whose form changed. */
+xeb_status xeb_plan_autotune(struct xeb_plan_s* plan, int reps, uintptr_t stream, int32_t* n_changed);
+
 xeb_status xeb_linear_xeb_noalloc(const double* amps_dev, size_t k, int n_qubits, double* out_dev,
                                   uintptr_t stream);
 

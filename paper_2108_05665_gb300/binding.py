@@ -94,6 +94,8 @@ _PROTOS = {
                                ctypes.c_void_p]),
     "xeb_plan_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_void_p]),
     "xeb_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "xeb_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_int32)]),
     "xeb_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp, _dblp, _dblp]),
     "xeb_linear_xeb_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p]),
@@ -261,6 +263,12 @@ def xeb_linear_xeb_noalloc(amps_dev_ptr: int, k: int, n_qubits: int, out_dev_ptr
 KERNEL_CLASSES = ["trie", "leaves", "permute", "gemm_tiled", "gemm_gemv", "gemm_tail", "gemm_generic",
                   "accum", "xeb", "gemm_tc", "gemm_stream", "gemm_memo"]
 XEB_N_KC = 16
+
+
+def xeb_plan_autotune(plan, reps: int, stream: int) -> int:
+    n = ctypes.c_int32()
+    _check(load().xeb_plan_autotune(plan, reps, stream, ctypes.byref(n)))
+    return n.value
 
 
 def xeb_plan_profile(plan, enable: bool):

@@ -41,6 +41,9 @@ int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 constexpr int GK_TC = 100;   // tcgen05 split-precision kernel, split W in smem (tc_gemm.cu)
 constexpr int GK_TC2 = 101;  // tcgen05 split-precision kernel, W^T in tensor memory (tc_gemm2.cu)
 
+// kernel-form choices of a contraction (autotuner candidates)
+enum Choice { CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_TC1 = 2, CH_GROUPED = 3, CH_SIMT = 4, CH_COUNT = 5 };
+
 struct GemmLaunch {
     CUtensorMap tmap;  // A of a TMA-mode tensor-core launch (64-byte aligned)
     int kernel;
@@ -285,6 +288,7 @@ struct xeb_plan_s {
     int64_t t_trie_desc = 0, t_internal = 0, t_leaf_desc = 0, t_pi = 0, t_bits = 0, t_acc = 0, t_amps = 0,
             t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0, t_sort = 0, t_memo = 0;
     size_t memo_bytes = 0;
+    std::vector<int> choice;   // per op: CH_AUTO or the autotuner's form
     int n_sms = 152;
     int64_t tables_bytes = 0;
     std::vector<xebk::TrieDesc> trie;
@@ -787,6 +791,53 @@ std::vector<char> leaf_host_data(xeb_plan_s* p) {
     return h;
 }
 
+// Kernel form of one contraction: CH_AUTO follows the options; the others
+// force a form (the autotuner's candidates).  False if the form does not fit.
+bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
+    char* tables = p->ws + p->off_tables;
+    const xebk::GemmDesc& d = g.d;
+    const bool tf32 = p->opts.precision == XEB_PREC_TF32X3;
+    auto tc_common = [&](bool grouped) {
+        g.tc.a_off = d.a_off;
+        g.tc.b_off = grouped ? 0 : d.b_off;
+        g.tc.c_off = d.c_off;
+        g.tc.wimg = reinterpret_cast<float*>(tables + p->t_wimg);
+        g.tc.err = reinterpret_cast<int32_t*>(tables + p->t_err);
+        std::memset(&g.tmap, 0, sizeof(g.tmap));
+    };
+    if (op.M == 1 && op.N == 1) {
+        g.kernel = xebk::GK_TAIL;
+        return ch == CH_AUTO || ch == CH_SIMT;
+    }
+    const bool smem_w = ch == CH_TC1 || (ch == CH_AUTO && p->opts.reserved[1] == 1);
+    const bool tc_ok = tf32 && (ch == CH_AUTO || ch == CH_TC2 || ch == CH_TC2_GATHER || ch == CH_TC1);
+    if (tc_ok && tc_tile(op, g.tc, smem_w ? 7 : xebk::kTc2RowBits, !smem_w)) {
+        g.kernel = smem_w ? GK_TC : GK_TC2;
+        tc_common(false);
+        const bool gather = ch == CH_TC2_GATHER || (ch == CH_AUTO && p->opts.reserved[3] == 1);
+        if (g.tc.tma && (gather || !encode_a_map(g.tc, reinterpret_cast<const float2*>(p->ws + p->off_arena), g.tmap)))
+            g.tc.tma = 0;
+        return !(ch == CH_TC2 && !g.tc.tma);   // CH_TC2 means the TMA form
+    }
+    if (tc_ok && ch != CH_AUTO) return false;
+    if (tf32 && (ch == CH_GROUPED || (ch == CH_AUTO && p->opts.reserved[1] != 1 && p->opts.reserved[4] == 1)) &&
+        tc_grouped(p->an, op, d, g.tc)) {
+        g.kernel = GK_TC2;
+        tc_common(true);
+        g.tc.grp_a = reinterpret_cast<const int64_t*>(tables + p->t_memo);
+        g.tc.bpack_off = (p->off_tables + p->t_memo + ((d.n_groups * 8 + 255) & ~int64_t(255))) / 8;
+        g.s = xebk::StreamDesc{};
+        return true;
+    }
+    if (ch != CH_AUTO && ch != CH_SIMT) return false;
+    if (stream_tile(op, p->elem, g.s))
+        g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
+    else if (op.N == 1) g.kernel = xebk::GK_GEMV;
+    else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;
+    else g.kernel = xebk::GK_GENERIC;
+    return true;
+}
+
 void build_launches(xeb_plan_s* p) {
     const Analysis& an = p->an;
     const Program& pr = p->prog;
@@ -900,36 +951,7 @@ void build_launches(xeb_plan_s* p) {
                 d.uL = d.uR = d.gstart = nullptr;
                 d.n_groups = 1;
             }
-            if (op.M == 1 && op.N == 1) g.kernel = xebk::GK_TAIL;
-            else if (p->opts.precision == XEB_PREC_TF32X3 && tc_tile(op, g.tc, p->opts.reserved[1] != 1 ? xebk::kTc2RowBits : 7,
-                                                                  p->opts.reserved[1] != 1)) {
-                g.kernel = p->opts.reserved[1] == 1 ? GK_TC : GK_TC2;
-                g.tc.a_off = d.a_off;
-                g.tc.b_off = d.b_off;
-                g.tc.c_off = d.c_off;
-                g.tc.wimg = reinterpret_cast<float*>(tables + p->t_wimg);
-                g.tc.err = reinterpret_cast<int32_t*>(tables + p->t_err);
-                std::memset(&g.tmap, 0, sizeof(g.tmap));
-                if (g.tc.tma && (p->opts.reserved[3] == 1 ||
-                                 !encode_a_map(g.tc, reinterpret_cast<const float2*>(p->ws + p->off_arena), g.tmap)))
-                    g.tc.tma = 0;
-            } else if (p->opts.precision == XEB_PREC_TF32X3 && p->opts.reserved[1] != 1 &&
-                       p->opts.reserved[4] == 1 && tc_grouped(p->an, op, d, g.tc)) {
-                g.kernel = GK_TC2;
-                g.tc.a_off = d.a_off;
-                g.tc.b_off = 0;
-                g.tc.c_off = d.c_off;
-                g.tc.wimg = reinterpret_cast<float*>(tables + p->t_wimg);
-                g.tc.err = reinterpret_cast<int32_t*>(tables + p->t_err);
-                g.tc.grp_a = reinterpret_cast<const int64_t*>(tables + p->t_memo);
-                g.tc.bpack_off = (p->off_tables + p->t_memo + ((d.n_groups * 8 + 255) & ~int64_t(255))) / 8;
-                std::memset(&g.tmap, 0, sizeof(g.tmap));
-                g.s = xebk::StreamDesc{};
-            } else if (stream_tile(op, p->elem, g.s))
-                g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
-            else if (op.N == 1) g.kernel = xebk::GK_GEMV;
-            else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;
-            else g.kernel = xebk::GK_GENERIC;
+            select_kernel(p, op, p->choice.empty() ? CH_AUTO : p->choice[i], g);
         }
     }
 }
@@ -1096,6 +1118,27 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
     return true;
 }
 
+// one contraction's kernel(s), as chosen by select_kernel
+template <typename T>
+cudaError_t launch_gemm_op(xeb_plan_s* p, const GemmLaunch& g, T* arena, char* tables, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (g.kernel == GK_TC) {
+        if constexpr (sizeof(T) == 8) e = xebk::launch_tc_gemm(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st);
+    } else if (g.kernel == GK_TC2) {
+        if constexpr (sizeof(T) == 8) {
+            if (g.tc.grp) e = xebk::launch_memo_prep<float2>(g.d, reinterpret_cast<float2*>(arena), tables + p->t_memo, st);
+            if (e == cudaSuccess) e = xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st);
+        }
+    } else if (g.kernel == xebk::GK_MEMO) {
+        e = xebk::launch_gemm_memo<T>(g.d, g.s, arena, tables + p->t_memo, st);
+    } else if (g.kernel == xebk::GK_STREAM) {
+        e = xebk::launch_gemm_stream<T>(g.d, g.s, arena, st);
+    } else {
+        e = xebk::launch_gemm<T>(g.kernel, g.d, arena, st);
+    }
+    return e;
+}
+
 template <typename T>
 xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
     const Analysis& an = p->an;
@@ -1129,23 +1172,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 static const int cls_of[6] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
                                               XEB_KC_GEMM_TAIL, XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO};
                 ProfScope ps(p, st, g.kernel >= GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by);
-                if (g.kernel == GK_TC) {
-                    if constexpr (sizeof(T) == 8)
-                        XEB_CUDA(xebk::launch_tc_gemm(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st));
-                } else if (g.kernel == GK_TC2) {
-                    if constexpr (sizeof(T) == 8) {
-                        if (g.tc.grp)
-                            XEB_CUDA(xebk::launch_memo_prep<float2>(g.d, reinterpret_cast<float2*>(arena),
-                                                                    tables + p->t_memo, st));
-                        XEB_CUDA(xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st));
-                    }
-                } else if (g.kernel == xebk::GK_MEMO) {
-                    XEB_CUDA(xebk::launch_gemm_memo<T>(g.d, g.s, arena, tables + p->t_memo, st));
-                } else if (g.kernel == xebk::GK_STREAM) {
-                    XEB_CUDA(xebk::launch_gemm_stream<T>(g.d, g.s, arena, st));
-                } else {
-                    XEB_CUDA(xebk::launch_gemm<T>(g.kernel, g.d, arena, st));
-                }
+                XEB_CUDA(launch_gemm_op<T>(p, g, arena, tables, st));
             }
         }
         {
@@ -1413,6 +1440,74 @@ extern "C" xeb_status xeb_plan_keys(xeb_plan_s* p, int node, int32_t* key, int32
     if (uR) XEB_CUDA(cudaMemcpyAsync(uR, tables + d.uR_off, size_t(d.kv) * 4, cudaMemcpyDeviceToHost, st));
     XEB_CUDA(cudaStreamSynchronize(st));
     return XEB_OK;
+}
+
+// Autotuner: time every distinct kernel form of every contraction on the
+// plan's own operands (filled by one step), keep the fastest.
+extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t stream, int32_t* n_changed) {
+    xeb_status s = check_bound(p);
+    if (s != XEB_OK) return s;
+    if (reps < 1) return fail(XEB_EINVAL, "reps < 1");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const Program& pr = p->prog;
+    if (p->choice.size() != pr.ops.size()) p->choice.assign(pr.ops.size(), CH_AUTO);
+    const bool was_prof = p->profiling;
+    p->profiling = false;
+    double2* amps = reinterpret_cast<double2*>(p->ws + p->off_tables + p->t_amps);
+    s = enqueue_step(p, amps, st);   // operands with realistic contents
+    p->profiling = was_prof;
+    if (s != XEB_OK) return s;
+    XEB_CUDA(cudaStreamSynchronize(st));
+    char* tables = p->ws + p->off_tables;
+    cudaEvent_t e0, e1;
+    XEB_CUDA(cudaEventCreate(&e0));
+    XEB_CUDA(cudaEventCreate(&e1));
+    int changed = 0;
+    std::string why;
+    for (size_t i = 0; i < pr.ops.size() && s == XEB_OK; ++i) {
+        if (pr.ops[i].kind == OP_PERM) continue;
+        const GemmLaunch keep = p->gemms[i];
+        std::vector<std::pair<float, int>> timed;
+        std::vector<std::pair<int, int>> seen;
+        for (int ch = 0; ch < CH_COUNT && s == XEB_OK; ++ch) {
+            GemmLaunch g = keep;
+            if (!select_kernel(p, pr.ops[i], ch, g)) continue;
+            const std::pair<int, int> form{g.kernel, g.kernel == GK_TC2 ? g.tc.tma + 2 * g.tc.grp : 0};
+            if (std::find(seen.begin(), seen.end(), form) != seen.end()) continue;
+            seen.push_back(form);
+            p->gemms[i] = g;
+            if (!validate_launches(p, why)) continue;
+            auto launch = [&]() {
+                return p->elem == 8 ? launch_gemm_op<float2>(p, g, reinterpret_cast<float2*>(p->ws + p->off_arena), tables, st)
+                                    : launch_gemm_op<double2>(p, g, reinterpret_cast<double2*>(p->ws + p->off_arena), tables, st);
+            };
+            cudaError_t e = launch();   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) s = fail(XEB_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            else timed.push_back({ms, ch});
+        }
+        p->gemms[i] = keep;
+        if (s != XEB_OK || timed.size() < 2) continue;
+        const auto best = *std::min_element(timed.begin(), timed.end());
+        GemmLaunch g = keep;
+        select_kernel(p, pr.ops[i], best.second, g);
+        const bool differs = g.kernel != keep.kernel || (g.kernel == GK_TC2 && (g.tc.tma != keep.tc.tma || g.tc.grp != keep.tc.grp));
+        p->choice[i] = best.second;
+        p->gemms[i] = g;
+        changed += differs;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == XEB_OK && !validate_launches(p, why)) s = fail(XEB_EINVAL, "autotuned launches failed validation: " + why);
+    drop_graph(p, p->graph_plain);   // recaptured with the new forms
+    for (auto& g : p->graph_prof) drop_graph(p, g);
+    if (n_changed) *n_changed = changed;
+    return s;
 }
 
 extern "C" xeb_status xeb_plan_profile(xeb_plan_s* p, int enable) {

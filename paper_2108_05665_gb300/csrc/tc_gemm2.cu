@@ -180,7 +180,7 @@ struct Sm2 {
 
 }  // namespace
 
-template <bool kTma>
+template <bool kTma, bool kGrp>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm2(const __grid_constant__ TcDesc t, const __grid_constant__ CUtensorMap tmap, float2* __restrict__ arena) {
     constexpr int kRing = op_stages<kTma>();
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* cst = reinterpret_cast<float*>(ring + kRing * kStageBytes);  // kRows x kCStride
     Sm2* S = reinterpret_cast<Sm2*>(cst + kRows * kCStride);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t n_tiles = t.grp ? t.n_groups * t.tpg : t.M / kRows;
+    const int64_t n_tiles = kGrp ? t.n_groups * t.tpg : t.M / kRows;
     const int nch = t.n_chunks;
     if (tid == 0) {
         for (int s = 0; s < kRing; ++s) {
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int64_t cg = -1, cga = 0;   // grouped mode: last group seen and its A offset
         auto tile_base = [&](int64_t tile) {
             int64_t b = 0;
-            if (t.grp) {
+            if constexpr (kGrp) {
                 const int64_t g = tile / t.tpg;
                 tile -= g * t.tpg;
                 if (g != cg) {
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int n = np >> 1, cpart = np & 1;
             bool live = np < t.N2;
             const float2* B = arena + t.b_off;
-            if (t.grp) {
+            if constexpr (kGrp) {
                 const int64_t g = tile / t.tpg;
                 const int64_t u0 = t.gstart[g];
                 live = np < 2 * (t.gstart[g + 1] - u0);
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // written after this tile's accumulators are read and before they
             // are released (the MMAs of this tile are complete by then)
             const int64_t nxt = tile + gridDim.x;
-            const bool switch_w = t.grp && nxt < n_tiles && nxt / t.tpg != tile / t.tpg;
+            const bool switch_w = kGrp && nxt < n_tiles && nxt / t.tpg != tile / t.tpg;
             // D^T: lane = output column np, column = tile row; tensor memory is
             // released for the next tile's MMAs once the last load has landed
             const uint32_t db = tmem + 256;
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__all_sync(0xffffffffu, epi_sync())) break;
             int64_t cbase = 0, mt = tile;
             int nk = 1 << 30;   // grouped mode: keys (columns) of this tile's group
-            if (t.grp) {
+            if constexpr (kGrp) {
                 const int64_t g = tile / t.tpg;
                 mt = tile - g * t.tpg;
                 const int64_t u0 = t.gstart[g];
@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if ((mt >> i) & 1) cbase += int64_t(1) << t.ext_cpos[i];
             float2* C = arena + t.c_off + cbase;
             const float2* st2 = reinterpret_cast<const float2*>(cst);
-            if (e_active) {
+            if (e_active && !kGrp) {
                 for (int jm = 0; jm < nmid; ++jm) {
                     int64_t gm = gq;
                     int sm2 = sq;
@@ -572,7 +572,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (j < nlo) v[j] = st2[sm2 + s8[j]];
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (j < nlo && (sm2 + s8[j]) % (kCStride / 2) < nk) C[gm + g8[j]] = v[j];
+                        if (j < nlo) C[gm + g8[j]] = v[j];
+                }
+            } else if (e_active) {   // grouped mode: only the group's nk key columns exist
+                for (int jm = 0; jm < nmid; ++jm) {
+                    int64_t gm = gq;
+                    int sm2 = sq;
+                    for (int bb = 0; bb < wb - lb; ++bb)
+                        if ((jm >> bb) & 1) {
+                            gm += ginc(5 + lb + bb);
+                            sm2 += sinc(5 + lb + bb);
+                        }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j < nlo && (sm2 + s8[j]) % (kCStride / 2) < nk) C[gm + g8[j]] = st2[sm2 + s8[j]];
                 }
             }
             if (!__all_sync(0xffffffffu, epi_sync())) break;
@@ -599,18 +612,22 @@ cudaError_t prepare_tc1();
 cudaError_t prepare_tc_kernels() {
     cudaError_t e = prepare_tc1();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_gemm2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<true>()));
+    e = cudaFuncSetAttribute(k_tc_gemm2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<true>()));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tc_gemm2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<false>()));
+    e = cudaFuncSetAttribute(k_tc_gemm2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<false>()));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tc_gemm2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<false>()));
 }
 
 cudaError_t launch_tc_gemm2(const TcDesc& t, const CUtensorMap& tmap, float2* arena, int n_sms, cudaStream_t st) {
-    const int64_t tiles = t.M / kRows;
+    const int64_t tiles = t.grp ? t.n_groups * t.tpg : t.M / kRows;
     const int grid = int(tiles < n_sms ? tiles : n_sms);
     if (t.tma)
-        k_tc_gemm2<true><<<grid, kThreads, tc2_smem<true>(), st>>>(t, tmap, arena);
+        k_tc_gemm2<true, false><<<grid, kThreads, tc2_smem<true>(), st>>>(t, tmap, arena);
+    else if (t.grp)
+        k_tc_gemm2<false, true><<<grid, kThreads, tc2_smem<false>(), st>>>(t, tmap, arena);
     else
-        k_tc_gemm2<false><<<grid, kThreads, tc2_smem<false>(), st>>>(t, tmap, arena);
+        k_tc_gemm2<false, false><<<grid, kThreads, tc2_smem<false>(), st>>>(t, tmap, arena);
     return cudaGetLastError();
 }
 

@@ -46,3 +46,26 @@ def test_grouped_memo_levels(grid4x6):
         assert abs(F - xeb.fidelity(ref, 24)) < TF32_F_TOL
         plan.close()
     assert res[0][2] == res[1][2] + 1   # the memo level ran as one grouped tensor-core launch
+
+
+def test_autotuned_plan_keeps_parity(grid4x6):
+    """The autotuner times every kernel form of every contraction and keeps
+    the fastest; the tuned plan must still meet the oracle bound."""
+    import torch
+    circ, bits, ref = grid4x6
+    o = B.xeb_default_opts()
+    o.precision = B.XEB_PREC_TF32X3
+    plan = B.Plan(circ, bits, opts=o).bind()
+    st = torch.cuda.current_stream().cuda_stream
+    dev = torch.from_numpy(np.asarray(bits, dtype=np.uint64).view(np.int64).copy()).cuda()
+    B.xeb_set_bitstrings(plan.handle, dev.data_ptr(), len(bits), st)
+    changed = B.xeb_plan_autotune(plan.handle, 2, st)
+    print("autotune changed %d contractions" % changed)
+    out = torch.empty(2 * len(bits), dtype=torch.float64, device="cuda")
+    B.xeb_set_bitstrings(plan.handle, dev.data_ptr(), len(bits), st)
+    B.xeb_amplitudes(plan.handle, out.data_ptr(), st)
+    F = B.xeb_fidelity(plan.handle, st)[0]
+    amps = out.cpu().numpy().view(np.complex128)
+    assert rel_err(amps, ref, 24).max() < AMP_TOL
+    assert abs(F - xeb.fidelity(ref, 24)) < TF32_F_TOL
+    plan.close()
