@@ -261,6 +261,41 @@ xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* la
  * device address (with the device current); make that first call before any
  * stream capture.  All calls share the array, so calls whose kernels overlap
  * on the GPU race. */
+/* ---- learned cost model ------------------------------------------------
+ * Candidates of the planner for a circuit and bitstring set: every tree the
+ * planner would weigh (greedy restarts, sweep family) with the slice set its
+ * slicing step gives it, and XEB_N_FEATURES features per candidate (exact
+ * counter totals over slices, the hand time model, per kernel class counts,
+ * bytes and flops).  Writes up to max_cands candidates: trees as
+ * [max_cands][n_leaves-1][2] (post-order pairs, as xeb_tree), slices as
+ * [max_cands][30] (-1 padded), n_sliced, features [max_cands][XEB_N_FEATURES]
+ * and the planner family (XEB_PLANNER_*); any output may be NULL.  n_out
+ * receives the number written.  Host only. */
+#define XEB_N_FEATURES 32
+xeb_status xeb_plan_candidates(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                               const xeb_plan_opts* opts, int max_cands, int32_t* trees, int32_t* slices,
+                               int32_t* n_sliced, double* features, int32_t* planner, int32_t* n_out);
+
+/* The model: n_layers hidden ReLU layers of n_hidden units and one linear
+ * output, predicting log2 of the step time from the features.  Parameters,
+ * gradients and Adam moments live on the device; parameters are laid out
+ * layer by layer as W_l (out x in, row-major) then b_l.  Inputs are
+ * normalised as (x - mean) * scale with xeb_mlp_set_norm.  Inputs and targets
+ * are float32 device arrays ([n][n_in], [n]).  Forward/train run on
+ * `stream`; xeb_mlp_gradients (mean squared error gradients to host, for
+ * checks) synchronises it. */
+struct xeb_mlp_s;
+xeb_status xeb_mlp_create(int n_in, int n_hidden, int n_layers, uint64_t seed, struct xeb_mlp_s** out);
+void xeb_mlp_destroy(struct xeb_mlp_s* mlp);
+size_t xeb_mlp_n_params(struct xeb_mlp_s* mlp);
+xeb_status xeb_mlp_weights(struct xeb_mlp_s* mlp, float* host, int set);   /* set = 1: upload, 0: download */
+xeb_status xeb_mlp_set_norm(struct xeb_mlp_s* mlp, const float* mean, const float* scale);
+xeb_status xeb_mlp_forward(struct xeb_mlp_s* mlp, const float* x_dev, int n, float* y_dev, uintptr_t stream);
+xeb_status xeb_mlp_gradients(struct xeb_mlp_s* mlp, const float* x_dev, const float* t_dev, int n,
+                             float* grad_host, float* loss_host, uintptr_t stream);
+xeb_status xeb_mlp_train_step(struct xeb_mlp_s* mlp, const float* x_dev, const float* t_dev, int n, float lr,
+                              float* loss_dev, uintptr_t stream);   /* one Adam step; loss_dev may be NULL */
+
 /* Autotuner (the plan's own form of "tile shapes picked by an autotuner"):
  * runs one step to fill the operands, then for every contraction times each
  * kernel form that fits it -- tcgen05 with TMA loads, tcgen05 with gathered

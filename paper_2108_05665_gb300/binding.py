@@ -94,6 +94,20 @@ _PROTOS = {
                                ctypes.c_void_p]),
     "xeb_plan_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_void_p]),
     "xeb_plan_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "xeb_plan_candidates": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]),
+    "xeb_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "xeb_mlp_destroy": (None, [ctypes.c_void_p]),
+    "xeb_mlp_n_params": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "xeb_mlp_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "xeb_mlp_set_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "xeb_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64]),
+    "xeb_mlp_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]),
+    "xeb_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_float, ctypes.c_void_p, ctypes.c_uint64]),
     "xeb_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_int32)]),
     "xeb_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp, _dblp, _dblp]),
@@ -263,6 +277,87 @@ def xeb_linear_xeb_noalloc(amps_dev_ptr: int, k: int, n_qubits: int, out_dev_ptr
 KERNEL_CLASSES = ["trie", "leaves", "permute", "gemm_tiled", "gemm_gemv", "gemm_tail", "gemm_generic",
                   "accum", "xeb", "gemm_tc", "gemm_stream", "gemm_memo"]
 XEB_N_KC = 16
+
+
+XEB_N_FEATURES = 32
+
+
+def xeb_plan_candidates(circuit, bitstrings, opts=None, max_cands: int = 256):
+    """Planner candidates: list of dicts with tree [(l, r)...], slices, features, planner."""
+    c = CircuitArrays(circuit)
+    bits = np.ascontiguousarray(bitstrings, dtype=np.uint64)
+    o = opts or xeb_default_opts()
+    n_leaves, _ = xeb_network_info(circuit)
+    nn = n_leaves - 1
+    trees = np.zeros((max_cands, nn, 2), dtype=np.int32)
+    slices = np.full((max_cands, 30), -1, dtype=np.int32)
+    nsl = np.zeros(max_cands, dtype=np.int32)
+    feats = np.zeros((max_cands, XEB_N_FEATURES), dtype=np.float64)
+    fam = np.zeros(max_cands, dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(load().xeb_plan_candidates(ctypes.byref(c.c), bits.ctypes.data_as(ctypes.c_void_p), len(bits),
+                                      ctypes.byref(o), max_cands, trees.ctypes.data_as(ctypes.c_void_p),
+                                      slices.ctypes.data_as(ctypes.c_void_p), nsl.ctypes.data_as(ctypes.c_void_p),
+                                      feats.ctypes.data_as(ctypes.c_void_p), fam.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(n)))
+    out = []
+    for i in range(n.value):
+        out.append({"tree": [tuple(int(x) for x in pr) for pr in trees[i]],
+                    "slices": [int(x) for x in slices[i, :nsl[i]]],
+                    "features": feats[i].copy(), "planner": int(fam[i])})
+    return out
+
+
+class Mlp:
+    """The learned cost model's network on the device (hand-written kernels)."""
+
+    def __init__(self, n_in=XEB_N_FEATURES, n_hidden=128, n_layers=3, seed=0):
+        h = ctypes.c_void_p()
+        _check(load().xeb_mlp_create(n_in, n_hidden, n_layers, seed, ctypes.byref(h)))
+        self.handle, self.n_in, self.n_hidden, self.n_layers = h.value, n_in, n_hidden, n_layers
+
+    def close(self):
+        if self.handle:
+            load().xeb_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_params(self):
+        return int(load().xeb_mlp_n_params(self.handle))
+
+    def get_weights(self):
+        w = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().xeb_mlp_weights(self.handle, w.ctypes.data_as(ctypes.c_void_p), 0))
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.n_params
+        _check(load().xeb_mlp_weights(self.handle, w.ctypes.data_as(ctypes.c_void_p), 1))
+
+    def set_norm(self, mean, scale):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        _check(load().xeb_mlp_set_norm(self.handle, m.ctypes.data_as(ctypes.c_void_p), sc.ctypes.data_as(ctypes.c_void_p)))
+
+    def forward(self, x_dev_ptr, n, y_dev_ptr, stream):
+        _check(load().xeb_mlp_forward(self.handle, x_dev_ptr, n, y_dev_ptr, stream))
+
+    def gradients(self, x_dev_ptr, t_dev_ptr, n, stream):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check(load().xeb_mlp_gradients(self.handle, x_dev_ptr, t_dev_ptr, n, g.ctypes.data_as(ctypes.c_void_p),
+                                        loss.ctypes.data_as(ctypes.c_void_p), stream))
+        return g, float(loss[0])
+
+    def train_step(self, x_dev_ptr, t_dev_ptr, n, lr, loss_dev_ptr, stream):
+        _check(load().xeb_mlp_train_step(self.handle, x_dev_ptr, t_dev_ptr, n, ctypes.c_float(lr), loss_dev_ptr, stream))
 
 
 def xeb_plan_autotune(plan, reps: int, stream: int) -> int:

@@ -482,6 +482,141 @@ bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& slic
     return true;
 }
 
+// Slicing (App. A, "Slicing"): while the arena exceeds the budget, add the
+// leg that minimises the objective f (memory penalty + log2 of the total
+// time over all slices); ties go to the smaller arena, then the smaller
+// largest tensor, then the smaller total tensor size.
+void slice_candidate(const Network& net, DistinctCounter& dc, const xeb_plan_opts& o, size_t elem, uint64_t k,
+                     Candidate& best, std::vector<int>& sliced, std::string& err) {
+        auto node_elems = [](const Analysis& an, int v) {
+            return double(an.nodes[v].kv) * std::ldexp(1.0, int(an.nodes[v].legs.size()));
+        };
+        auto measure = [&](const Candidate& c) {
+            double mx = 0, tot = 0;
+            for (size_t v = 0; v < c.an.nodes.size(); ++v) {
+                const double e = node_elems(c.an, int(v));
+                mx = std::max(mx, e);
+                tot += e;
+            }
+            return std::array<double, 4>{c.f, double(c.arena_bytes), mx, tot};
+        };
+        while (uint64_t(best.arena_bytes) > o.mem_budget && sliced.size() < 30) {
+            const auto mb = measure(best);
+            std::vector<int> legs;
+            for (size_t v = 0; v < best.an.nodes.size(); ++v)
+                if (node_elems(best.an, int(v)) * 2 >= mb[2])
+                    for (int l : best.an.nodes[v].legs)
+                        if (std::find(legs.begin(), legs.end(), l) == legs.end()) legs.push_back(l);
+            Candidate bc;
+            std::array<double, 4> bm{};
+            int bl = -1;
+            for (int l : legs) {
+                std::vector<int> s2 = sliced;
+                s2.push_back(l);
+                Candidate c;
+                if (!evaluate(net, best.tree, s2, dc, o, elem, k, c, err)) continue;
+                const auto m = measure(c);
+                if (bl < 0 || m < bm) {
+                    bc = std::move(c);
+                    bm = m;
+                    bl = l;
+                }
+            }
+            if (bl < 0 || !(bm < mb)) break;
+            sliced.push_back(bl);
+            best = std::move(bc);
+        }
+    }
+
+// The planner's candidate trees: randomised greedy restarts and the sweep
+// family (body blocks of b qubits, output leaves in groups of G, two variants).
+std::vector<std::pair<int, Tree>> candidate_trees(const Network& net, DistinctCounter& dc,
+                                                  const std::vector<int>& sliced, const xeb_plan_opts& o) {
+    std::vector<std::pair<int, Tree>> cands;
+        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_GREEDY) {
+            const int trials = std::max(1, o.greedy_trials);
+            for (int t = 0; t < trials; ++t)
+                cands.push_back({XEB_PLANNER_GREEDY, greedy_tree(net, dc, sliced, o.seed + t, t == 0 ? 0.0 : 0.15)});
+        }
+        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_SWEEP) {
+            std::vector<int> bs, gs;
+            if (o.block_qubits > 0) bs = {o.block_qubits};
+            else for (int b = 2; b <= 10; ++b) bs.push_back(b);
+            if (o.group_leaves > 0) gs = {o.group_leaves};
+            else gs = {1, 2, 3, 4};
+            for (int variant = 0; variant < 2; ++variant)
+                for (int b : bs)
+                    for (int g : gs) {
+                        Tree t;
+                        if (sweep_tree(net, b, g, t, variant)) cands.push_back({XEB_PLANNER_SWEEP, t});
+                    }
+        }
+    return cands;
+}
+
+// Plan features of the learned cost model (XEB_N_FEATURES values): exact
+// counter totals over all slices, the hand time model, and per kernel class
+// (as the default kernel selection assigns them: tensor core, streaming,
+// memo level, tiled, small) the count, bytes and flops of its contractions.
+void plan_features(const Candidate& c, size_t n_sliced, const xeb_plan_opts& o, size_t elem, uint64_t k, int n,
+                   double* f) {
+    for (int i = 0; i < XEB_N_FEATURES; ++i) f[i] = 0;
+    auto lg = [](double x) { return std::log2(1.0 + std::max(0.0, x)); };
+    const double nsl = std::ldexp(1.0, int(n_sliced));
+    const bool tf32 = o.precision == XEB_PREC_TF32X3;
+    double cls_n[5] = {0}, cls_b[5] = {0}, cls_f[5] = {0};
+    double tot_b = 0, tot_f = 0, b_k4 = 0, b_n4 = 0, b_small_m = 0, max_e = 0, max_kv = 0, tot_e = 0;
+    for (const Op& op : c.prog.ops) {
+        if (op.kind == OP_PERM) continue;
+        const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
+        const double by = double(elem) * (double(c.an.nodes[op.a_node].kv) * double(op.M * op.K) +
+                                          double(c.an.nodes[op.b_node].kv) * double(op.K * op.N) +
+                                          double(op.kv) * double(op.M * op.N));
+        xebk::StreamDesc sd;
+        int cl;
+        if (tf32 && tc_eligible(op)) cl = 0;
+        else if (stream_tile(op, elem, sd)) cl = (op.N == 1 && op.kv > 1) ? 2 : 1;
+        else if (op.N > 1 && op.M >= 16 && op.N >= 16) cl = 3;
+        else cl = 4;
+        cls_n[cl] += 1;
+        cls_b[cl] += by;
+        cls_f[cl] += fl;
+        tot_b += by;
+        tot_f += fl;
+        if (op.K <= 4) b_k4 += by;
+        if (op.N <= 4) b_n4 += by;
+        if (op.M < 4096) b_small_m += by;
+    }
+    for (const auto& nd : c.an.nodes) {
+        const double e = double(nd.kv) * std::ldexp(1.0, int(nd.legs.size()));
+        max_e = std::max(max_e, e);
+        max_kv = std::max(max_kv, double(nd.kv));
+        tot_e += e;
+    }
+    f[0] = lg(c.costs.C * nsl);
+    f[1] = lg(c.costs.RW * nsl);
+    f[2] = lg(c.costs.perm * nsl);
+    f[3] = double(n_sliced);
+    f[4] = lg(double(c.arena_bytes));
+    f[5] = lg(1e6 * nsl * estimate_time(c.an, c.prog, o.precision, elem));
+    f[6] = lg(double(c.prog.ops.size()));
+    f[7] = lg(double(k));
+    f[8] = double(n);
+    for (int cl = 0; cl < 5; ++cl) {
+        f[9 + 3 * cl] = lg(cls_n[cl] * nsl);
+        f[10 + 3 * cl] = lg(cls_b[cl] * nsl);
+        f[11 + 3 * cl] = lg(cls_f[cl] * nsl);
+    }
+    f[24] = lg(max_e);
+    f[25] = lg(max_kv);
+    f[26] = tot_b > 0 ? b_k4 / tot_b : 0;
+    f[27] = tot_b > 0 ? b_n4 / tot_b : 0;
+    f[28] = lg(tot_e * nsl);
+    f[29] = tf32 ? 1.0 : 0.0;
+    f[30] = tot_f > 0 ? cls_f[0] / tot_f : 0;
+    f[31] = lg(b_small_m * nsl);
+}
+
 }  // namespace
 
 extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
@@ -525,25 +660,7 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         p->planner_used = 0;
     } else {
         if (p->net.leaves.size() < 2) return fail(XEB_EUNSUPPORTED, "network with fewer than two leaves");
-        std::vector<std::pair<int, Tree>> cands;
-        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_GREEDY) {
-            const int trials = std::max(1, o.greedy_trials);
-            for (int t = 0; t < trials; ++t)
-                cands.push_back({XEB_PLANNER_GREEDY, greedy_tree(p->net, dc, p->sliced, o.seed + t, t == 0 ? 0.0 : 0.15)});
-        }
-        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_SWEEP) {
-            std::vector<int> bs, gs;
-            if (o.block_qubits > 0) bs = {o.block_qubits};
-            else for (int b = 2; b <= 10; ++b) bs.push_back(b);
-            if (o.group_leaves > 0) gs = {o.group_leaves};
-            else gs = {1, 2, 3, 4};
-            for (int variant = 0; variant < 2; ++variant)
-                for (int b : bs)
-                    for (int g : gs) {
-                        Tree t;
-                        if (sweep_tree(p->net, b, g, t, variant)) cands.push_back({XEB_PLANNER_SWEEP, t});
-                    }
-        }
+        std::vector<std::pair<int, Tree>> cands = candidate_trees(p->net, dc, p->sliced, o);
         for (auto& c : cands) {
             Candidate cd_;
             if (!evaluate(p->net, c.second, p->sliced, dc, o, p->elem, k, cd_, err)) continue;
@@ -555,57 +672,61 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         }
         if (!have) return fail(XEB_EINVAL, "planner found no valid tree: " + err);
     }
-    // slicing (App. A, "Slicing"): while the arena exceeds the budget, add the
-    // leg that minimises the objective f (memory penalty + log2 of the total
-    // time over all slices), so a leg that shrinks memory without multiplying
-    // the work is preferred; ties go to the smaller arena, then the smaller
-    // largest tensor, then the smaller total tensor size.
-    if (!slices) {
-        auto node_elems = [](const Analysis& an, int v) {
-            return double(an.nodes[v].kv) * std::ldexp(1.0, int(an.nodes[v].legs.size()));
-        };
-        auto measure = [&](const Candidate& c) {
-            double mx = 0, tot = 0;
-            for (size_t v = 0; v < c.an.nodes.size(); ++v) {
-                const double e = node_elems(c.an, int(v));
-                mx = std::max(mx, e);
-                tot += e;
-            }
-            return std::array<double, 4>{c.f, double(c.arena_bytes), mx, tot};
-        };
-        while (uint64_t(best.arena_bytes) > o.mem_budget && p->sliced.size() < 30) {
-            const auto mb = measure(best);
-            std::vector<int> legs;
-            for (size_t v = 0; v < best.an.nodes.size(); ++v)
-                if (node_elems(best.an, int(v)) * 2 >= mb[2])
-                    for (int l : best.an.nodes[v].legs)
-                        if (std::find(legs.begin(), legs.end(), l) == legs.end()) legs.push_back(l);
-            Candidate bc;
-            std::array<double, 4> bm{};
-            int bl = -1;
-            for (int l : legs) {
-                std::vector<int> s2 = p->sliced;
-                s2.push_back(l);
-                Candidate c;
-                if (!evaluate(p->net, best.tree, s2, dc, o, p->elem, k, c, err)) continue;
-                const auto m = measure(c);
-                if (bl < 0 || m < bm) {
-                    bc = std::move(c);
-                    bm = m;
-                    bl = l;
-                }
-            }
-            if (bl < 0 || !(bm < mb)) break;
-            p->sliced.push_back(bl);
-            best = std::move(bc);
-        }
-    }
+    if (!slices) slice_candidate(p->net, dc, o, p->elem, k, best, p->sliced, err);
     p->tree = best.tree;
     p->an = std::move(best.an);
     p->prog = std::move(best.prog);
     p->costs = best.costs;
     p->objective = best.f;
     *out = p.release();
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_candidates(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                                          const xeb_plan_opts* opts, int max_cands, int32_t* trees,
+                                          int32_t* slices, int32_t* n_sliced, double* features, int32_t* planner,
+                                          int32_t* n_out) {
+    if (!n_out) return fail(XEB_EINVAL, "n_out is NULL");
+    *n_out = 0;
+    if (k == 0 || !bitstrings) return fail(XEB_EINVAL, "need k >= 1 bitstrings");
+    if (k > size_t(xebk::kMaxK)) return fail(XEB_EUNSUPPORTED, "too many bitstrings");
+    xeb_plan_opts o;
+    if (opts) o = *opts;
+    else xeb_default_opts(&o);
+    const size_t elem = o.precision == XEB_PREC_FP64 ? 16 : 8;
+    Network net;
+    std::string err;
+    if (!build_network(circuit, net, err)) return fail(XEB_EINVAL, err);
+    if (net.leaves.size() < 2) return fail(XEB_EUNSUPPORTED, "network with fewer than two leaves");
+    std::vector<uint64_t> bits(bitstrings, bitstrings + k);
+    for (uint64_t b : bits)
+        if (net.n < 64 && (b >> net.n) != 0) return fail(XEB_EINVAL, "bitstring has bits above n");
+    DistinctCounter dc;
+    dc.bs = bits.data();
+    dc.k = k;
+    const std::vector<int> none;
+    const auto cands = candidate_trees(net, dc, none, o);
+    const int nn = int(net.leaves.size()) - 1;
+    int w = 0;
+    for (const auto& c : cands) {
+        if (w >= max_cands) break;
+        Candidate cd;
+        if (!evaluate(net, c.second, none, dc, o, elem, k, cd, err)) continue;
+        std::vector<int> sl;
+        slice_candidate(net, dc, o, elem, k, cd, sl, err);
+        if (trees)
+            for (int i = 0; i < nn; ++i) {
+                trees[(size_t(w) * nn + i) * 2] = cd.tree[i][0];
+                trees[(size_t(w) * nn + i) * 2 + 1] = cd.tree[i][1];
+            }
+        if (slices)
+            for (int i = 0; i < 30; ++i) slices[size_t(w) * 30 + i] = i < int(sl.size()) ? sl[i] : -1;
+        if (n_sliced) n_sliced[w] = int(sl.size());
+        if (planner) planner[w] = c.first;
+        if (features) plan_features(cd, sl.size(), o, elem, k, net.n, features + size_t(w) * XEB_N_FEATURES);
+        ++w;
+    }
+    *n_out = w;
     return XEB_OK;
 }
 

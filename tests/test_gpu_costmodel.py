@@ -1,0 +1,131 @@
+"""The learned cost model's hand-written kernels against the NumPy reference
+network: forward values, loss gradients, one Adam step, and training that
+fits a known function."""
+import numpy as np
+import pytest
+
+from paper_2108_05665_gb300 import binding as B, build
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (32, 128, 3)   # features, hidden units, hidden layers (the planner's model)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    build.build()
+    B.load()
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 3, (n, DIMS[0])).astype(np.float32) + 10
+    t = (np.sin(X[:, 0] / 3) + 0.1 * X[:, 1] - 0.05 * X[:, 2] * X[:, 3] / 10).astype(np.float32)
+    mean = X.mean(0).astype(np.float32)
+    scale = (1 / X.std(0)).astype(np.float32)
+    return X, t, mean, scale
+
+
+def test_forward_and_gradients_match_reference():
+    import torch
+    X, t, mean, scale = _data(300, 1)   # 300 rows: ragged tail of the 16-row tiles
+    m = B.Mlp(*DIMS, seed=3)
+    m.set_norm(mean, scale)
+    w = m.get_weights().astype(np.float64)
+    sp = torch.cuda.current_stream().cuda_stream
+    Xd = torch.from_numpy(X).cuda()
+    td = torch.from_numpy(t).cuda()
+    yd = torch.empty(len(X), dtype=torch.float32, device="cuda")
+    m.forward(Xd.data_ptr(), len(X), yd.data_ptr(), sp)
+    y = yd.cpu().numpy()
+    y_ref = ref.forward(w, mean.astype(np.float64), scale.astype(np.float64), X, *DIMS)[-1][:, 0]
+    assert np.max(np.abs(y - y_ref)) <= 1e-4 * max(1.0, np.max(np.abs(y_ref)))
+    g, loss = m.gradients(Xd.data_ptr(), td.data_ptr(), len(X), sp)
+    g_ref = ref.gradients(w, mean.astype(np.float64), scale.astype(np.float64), X, t, *DIMS)
+    assert abs(loss - ref.loss(w, mean.astype(np.float64), scale.astype(np.float64), X, t, *DIMS)) < 1e-4 * max(1, loss)
+    err = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert err < 1e-4, err
+    m.close()
+
+
+def test_adam_step_matches_reference():
+    import torch
+    X, t, mean, scale = _data(64, 2)
+    m = B.Mlp(*DIMS, seed=4)
+    m.set_norm(mean, scale)
+    w0 = m.get_weights().astype(np.float64)
+    sp = torch.cuda.current_stream().cuda_stream
+    Xd = torch.from_numpy(X).cuda()
+    td = torch.from_numpy(t).cuda()
+    m.train_step(Xd.data_ptr(), td.data_ptr(), len(X), 1e-3, 0, sp)
+    w1 = m.get_weights().astype(np.float64)
+    g = ref.gradients(w0, mean.astype(np.float64), scale.astype(np.float64), X, t, *DIMS)
+    w_ref, _, _ = ref.adam_step(w0, g, np.zeros_like(w0), np.zeros_like(w0), 1, 1e-3)
+    # first Adam step moves every parameter by ~lr * sign(g); compare where g is not tiny
+    sel = np.abs(g) > 1e-5 * np.abs(g).max()
+    assert np.max(np.abs(w1 - w_ref)[sel]) < 2e-5
+    m.close()
+
+
+def test_training_fits_a_known_function():
+    import torch
+    X, t, mean, scale = _data(4096, 5)
+    m = B.Mlp(*DIMS, seed=6)
+    m.set_norm(mean, scale)
+    sp = torch.cuda.current_stream().cuda_stream
+    Xd = torch.from_numpy(X).cuda()
+    td = torch.from_numpy(t).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    first = None
+    rng = np.random.default_rng(0)
+    for ep in range(60):
+        loss.zero_()
+        perm = torch.from_numpy(rng.permutation(len(X))).cuda()
+        for b0 in range(0, len(X), 256):
+            idx = perm[b0:b0 + 256]
+            m.train_step(Xd[idx].contiguous().data_ptr(), td[idx].contiguous().data_ptr(), len(idx), 1e-3,
+                         loss.data_ptr(), sp)
+        ep_loss = float(loss.item()) / 16
+        first = first if first is not None else ep_loss
+    var = float(np.var(t))
+    print("first epoch loss %.4f, last %.4f, target variance %.4f" % (first, ep_loss, var))
+    assert ep_loss < 0.1 * var
+    m.close()
+
+
+def test_learned_planner_choice_on_held_out_circuit():
+    """The trained model (committed weights) proposes plans for a circuit it
+    was not trained on; the verified choice is timed against the plain
+    planner's plan and its amplitudes still match the oracle."""
+    import os
+    from paper_2108_05665_gb300 import costmodel, inputs
+    from oracle import statevec
+    from gpu_util import rel_err
+    w = os.path.join(os.path.dirname(costmodel.__file__), "costmodel_weights.npz")
+    model = costmodel.CostModel.load(w)
+    circ = inputs.random_grid_circuit(4, 4, 10, 424242)
+    bits = inputs.uniform_bitstrings(16, 300, 434343)
+    o = B.xeb_default_opts()
+    o.precision = B.XEB_PREC_TF32X3
+    cands = B.xeb_plan_candidates(circ, bits, o)
+    pred = model.predict(np.array([c["features"] for c in cands]))
+    assert np.all(np.isfinite(pred))
+    ch = costmodel.choose_verified(circ, bits, o, model, top=3)
+    plain = B.Plan(circ, bits, opts=o)
+    tree, slices = plain.tree()
+    plain.close()
+    t_plain = costmodel.time_plan(circ, bits, tree, slices, o)
+    print("plain %.3f ms, verified %.3f ms (%s)" % (t_plain, ch["measured_ms"], ch["source"]))
+    assert ch["measured_ms"] <= 1.10 * t_plain
+    plan = B.Plan(circ, bits, tree=ch["tree"], slices=ch["slices"] or None, opts=o).bind()
+    import torch
+    st = torch.cuda.current_stream().cuda_stream
+    hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
+    ha = torch.empty(2 * len(bits), dtype=torch.float64).pin_memory()
+    B.xeb_run(plan.handle, hb.data_ptr(), len(bits), ha.data_ptr(), st)
+    amps = ha.numpy().view(np.complex128)
+    assert rel_err(amps, statevec.amplitudes(circ, bits), 16).max() < 1e-5
+    plan.close()
