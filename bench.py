@@ -210,6 +210,9 @@ def main():
                     help="launch the step kernel by kernel instead of replaying one captured CUDA graph")
     ap.add_argument("--tc-variant", default="tmem", choices=["tmem", "smem"],
                     help="tensor-core kernel: B^T in tensor memory (default) or split B in shared memory")
+    ap.add_argument("--planner", default="plain", choices=["plain", "learned"],
+                    help="plain: the planner's own objective; learned: the cost model's top candidates and the "
+                         "plain plan are timed and the fastest kept (plan-time, outside the timed region)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time every kernel form of every contraction this many times and keep the fastest "
                          "(plan-time, outside the timed region; 0 = off)")
@@ -236,8 +239,16 @@ def main():
     o.reserved[1] = 1 if args.tc_variant == "smem" else 0
     o.reserved[2] = 1 if args.eager else 0
     o.reserved[3] = 1 if args.tc_loads == "gather" else 0
+    chosen = None
+    if args.planner == "learned":
+        from paper_2108_05665_gb300 import costmodel
+        wpath = os.path.join(os.path.dirname(os.path.abspath(costmodel.__file__)), "costmodel_weights.npz")
+        chosen = costmodel.choose_verified(circ, bits, o, costmodel.CostModel.load(wpath), top=3, reps=2)
     try:
-        plan = B.Plan(circ, bits, opts=o)
+        if chosen is not None:
+            plan = B.Plan(circ, bits, tree=chosen["tree"], slices=chosen["slices"] or None, opts=o)
+        else:
+            plan = B.Plan(circ, bits, opts=o)
         plan.bind()
     except B.XebError as e:
         if prec == B.XEB_PREC_TF32X3 and e.status == 5:
@@ -340,7 +351,9 @@ def main():
                    "autotune": ("%d reps per form, %d contractions changed form" % (args.autotune, tuned))
                    if tuned is not None else "off",
                    "launch": "kernel by kernel" if args.eager else "one CUDA graph per step",
-                   "planner": ["given", "greedy", "sweep"][st["planner_used"]], "n_slices": st["n_slices"],
+                   "planner": ["given", "greedy", "sweep"][st["planner_used"]] if chosen is None
+                   else "learned cost model (%s plan kept after timing)" % chosen["source"],
+                   "n_slices": st["n_slices"],
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
                    "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},
         "complex_tflops": eff_tflops,
