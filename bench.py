@@ -219,8 +219,15 @@ def main():
     ap.add_argument("--tc-loads", default="tma", choices=["tma", "gather"],
                     help="tensor-core A operand: TMA boxes where A is row-major (default) or plain-load gathers")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid5x5_m12_k2000", "grid3x9_m12_k2000"],
-                    help="benchmark workload (default) or the small profiling case")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid5x5_m12_k2000", "grid3x9_m12_k2000",
+                                                          "grid5x8_m12_k100000", "grid6x9m1_m12_k300000",
+                                                          "grid6x9m1_m14_k1000000"],
+                    help="benchmark workload (default), the small profiling cases, or the sliced 40/53-qubit ones")
+    ap.add_argument("--slice-frac", type=float, default=None,
+                    help="run a seeded subset of the slices (partial sums) and extrapolate amplitudes/s by 1/frac; "
+                         "default: all slices, except 1/16 (40 qubits) and 1%% (53 qubits)")
+    ap.add_argument("--mem-gb", type=float, default=None,
+                    help="planner memory budget in GB (default 64 GiB; 200 for the 53-qubit workloads)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -239,6 +246,13 @@ def main():
     o.reserved[1] = 1 if args.tc_variant == "smem" else 0
     o.reserved[2] = 1 if args.eager else 0
     o.reserved[3] = 1 if args.tc_loads == "gather" else 0
+    big = w.n_qubits > 30
+    if args.mem_gb is not None:
+        o.mem_budget = int(args.mem_gb * 2 ** 30)
+    elif w.n_qubits > 40:
+        o.mem_budget = 200 << 30
+    if args.slice_frac is None and big:
+        args.slice_frac = 1.0 / 16 if w.n_qubits <= 40 else 0.01
     chosen = None
     if args.planner == "learned":
         from paper_2108_05665_gb300 import costmodel
@@ -265,6 +279,11 @@ def main():
     dev_bits = torch.from_numpy(bits.view(np.int64).copy()).cuda()
     out = torch.empty(2 * k, dtype=torch.float64, device="cuda")
 
+    frac = 1.0
+    n_run = st["n_slices"]
+    if args.slice_frac is not None and args.slice_frac < 1.0:
+        n_run = B.xeb_set_slice_subset(plan.handle, args.slice_frac, 12345)
+        frac = n_run / st["n_slices"]
     tuned = None
     if args.autotune > 0:
         B.xeb_set_bitstrings(plan.handle, dev_bits.data_ptr(), k, sp)
@@ -295,7 +314,7 @@ def main():
     ms_total = ev0.elapsed_time(ev1)
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    value = world * k * args.steps / (ms_total / 1e3)
+    value = world * k * args.steps / (ms_total / 1e3) * frac
     clocks = clk.summary()
     # ---- end-to-end through the host entry point (pinned host buffers) ----
     hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
@@ -309,7 +328,7 @@ def main():
         Fe = B.xeb_run(plan.handle, hb.data_ptr(), k, ha.data_ptr(), sp)
     torch.cuda.synchronize()
     e_s = max_over_ranks(time.perf_counter() - e0, world)
-    e2e_value = world * k * e_steps / e_s
+    e2e_value = world * k * e_steps / e_s * frac
     # ---- roofline of the dominant kernel class ----
     pk, pk_kind = peaks()
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -339,7 +358,7 @@ def main():
         peak = hbm
         peak_note = "measured copy bandwidth (" + pk_kind + ")"
     traffic = tc_traffic_per_launch(d["bytes"] / d["launches"]) if name == "gemm_tc" else None
-    eff_tflops = st["flops_per_slice"] * st["n_slices"] * args.steps * world / (ms_total / 1e3) / 1e12
+    eff_tflops = st["flops_per_slice"] * n_run * args.steps * world / (ms_total / 1e3) / 1e12
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
@@ -351,15 +370,19 @@ def main():
                    "autotune": ("%d reps per form, %d contractions changed form" % (args.autotune, tuned))
                    if tuned is not None else "off",
                    "launch": "kernel by kernel" if args.eager else "one CUDA graph per step",
-                   "planner": ["given", "greedy", "sweep"][st["planner_used"]] if chosen is None
+                   "planner": ["given", "greedy", "sweep", "anneal"][st["planner_used"]] if chosen is None
                    else "learned cost model (%s plan kept after timing)" % chosen["source"],
                    "n_slices": st["n_slices"],
+                   "slices_run": ("%d of %d (seeded subset, seed 12345; amplitudes/s extrapolated by "
+                                  "%d/%d; the outputs are partial sums)" % (n_run, st["n_slices"],
+                                                                            n_run, st["n_slices"]))
+                   if frac < 1.0 else "all",
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
                    "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},
         "complex_tflops": eff_tflops,
-        "flops_per_step": st["flops_per_slice"] * st["n_slices"],
+        "flops_per_step": st["flops_per_slice"] * n_run,
         "memo_gain": st["single_amp_flops"] / max(st["flops_per_slice"], 1.0),
-        "F": F, "F_e2e": Fe,
+        "F": F if frac >= 1.0 else None, "F_e2e": Fe if frac >= 1.0 else None,
         "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * k,
                 "d2h_bytes_per_step": 16 * k + 32},
         "gpu_launches": int(round(launches_per_step * args.steps)),

@@ -75,7 +75,11 @@ enum {
 enum {
     XEB_PLANNER_AUTO = 0,
     XEB_PLANNER_GREEDY = 1,  /* memo-aware greedy pairwise merging             */
-    XEB_PLANNER_SWEEP = 2    /* time-ordered body of gate blocks + output trie */
+    XEB_PLANNER_SWEEP = 2,   /* time-ordered body of gate blocks + output trie */
+    XEB_PLANNER_ANNEAL = 3   /* the best of the above refined by the local
+                                search of App. A (tree rewrites + slicing
+                                moves); AUTO also runs it when the constructed
+                                trees needed slicing                          */
 };
 
 typedef struct {
@@ -122,6 +126,8 @@ typedef struct {
                              [4] = 1: memo-trie levels with long groups run as
                              grouped tensor-core GEMMs (default: the SIMT
                              memo-level kernel, faster for K = 16 tiles);
+                             [5] = local-search proposals in thousands
+                             (0: 2000 per leaf);
                              others 0 */
 } xeb_plan_opts;
 
@@ -200,6 +206,24 @@ xeb_status xeb_set_bitstrings(struct xeb_plan_s* plan, const uint64_t* bitstring
  * captures the step as a CUDA graph on a private stream; later calls replay
  * it on `stream` (not while profiling, or with opts.reserved[2] = 1). */
 xeb_status xeb_amplitudes(struct xeb_plan_s* plan, double* out_dev, uintptr_t stream);
+
+/* Restrict the slice loop of xeb_amplitudes to a seeded subset of the
+ * 2^|S| slice values (App. A, "Slicing": an amplitude is the sum over all
+ * values of the sliced legs; a subset gives a partial sum -- not an
+ * amplitude -- used to time and check plans whose full sum takes too long).
+ * The subset holds max(1, round(frac * 2^|S|)) values: the first ones of a
+ * partial Fisher-Yates shuffle of 0 .. 2^|S|-1 whose draws are successive
+ * outputs of splitmix64 started at `seed` (draw j uses x mod (2^|S| - j)).
+ * frac >= 1 restores the full sum.  *n_chosen (may be NULL) receives the
+ * subset size; XEB_EINVAL for frac <= 0 or a subset above 2^26 values.  The
+ * next xeb_amplitudes call recaptures its graph. */
+xeb_status xeb_set_slice_subset(struct xeb_plan_s* plan, double frac, uint64_t seed, int64_t* n_chosen);
+
+/* The slice values the loop runs, in loop order (the subset's, else all
+ * 0 .. 2^|S|-1); ids needs room for the count xeb_set_slice_subset returned
+ * (2^|S| without a subset).  Bit b of a value is the value of sliced leg b in
+ * the order xeb_plan_tree reports the sliced legs. */
+xeb_status xeb_plan_slice_ids(const struct xeb_plan_s* plan, int64_t* ids);
 
 /* Linear XEB of the last xeb_amplitudes call (Eq. 1): F, mean of 2^n p and
  * mean of (2^n p)^2 over the sequence; host outputs; synchronises. */

@@ -166,9 +166,9 @@ def pair_contract(a: np.ndarray, la: Sequence[int], b: np.ndarray,
                   lb: Sequence[int]):
     """T*S of Eq. (elem-cont): sum over the legs the two tensors share.
     Result legs: a's unshared legs, then b's unshared legs."""
-    shared = set(la) & set(lb)
+    shared = [l for l in la if l in set(lb)]
     out = [l for l in la if l not in shared] + [l for l in lb if l not in shared]
-    ids = {l: i for i, l in enumerate(dict.fromkeys(list(la) + list(lb)))}
-    r = np.einsum(a, [ids[l] for l in la], b, [ids[l] for l in lb],
-                  [ids[l] for l in out])
+    # the sum over the shared legs as one matrix product (library tensordot)
+    r = np.tensordot(a, b, axes=([list(la).index(l) for l in shared],
+                                 [list(lb).index(l) for l in shared]))
     return r, out

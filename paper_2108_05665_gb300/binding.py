@@ -25,6 +25,7 @@ XEB_PREC_FP64 = 2
 XEB_PLANNER_AUTO = 0
 XEB_PLANNER_GREEDY = 1
 XEB_PLANNER_SWEEP = 2
+XEB_PLANNER_ANNEAL = 3
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -113,6 +114,9 @@ _PROTOS = {
     "xeb_plan_profile_read": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp, _dblp, _dblp]),
     "xeb_linear_xeb_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "xeb_set_slice_subset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64,
+                                            ctypes.POINTER(ctypes.c_int64)]),
+    "xeb_plan_slice_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "xeb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -244,6 +248,19 @@ def xeb_set_bitstrings(plan, bits_dev_ptr: int, k: int, stream: int):
 
 def xeb_amplitudes(plan, out_dev_ptr: int, stream: int):
     _check(load().xeb_amplitudes(plan, ctypes.c_void_p(out_dev_ptr or None), ctypes.c_void_p(stream or None)))
+
+
+def xeb_set_slice_subset(plan, frac: float, seed: int) -> int:
+    """Run only a seeded subset of the slice values (partial sums); returns its size."""
+    n = ctypes.c_int64()
+    _check(load().xeb_set_slice_subset(plan, float(frac), int(seed), ctypes.byref(n)))
+    return n.value
+
+
+def xeb_plan_slice_ids(plan, n: int) -> np.ndarray:
+    ids = np.zeros(n, dtype=np.int64)
+    _check(load().xeb_plan_slice_ids(plan, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return ids
 
 
 def xeb_fidelity(plan, stream: int):

@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         objs.append(obj)
     for src in cpps:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-I", INCLUDE, "-I", CSRC,
                "-I", os.path.join(CUDA_HOME, "include"), "-c", src, "-o", obj]
         jobs.append(cmd)
         objs.append(obj)

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.cuh"
@@ -289,6 +290,7 @@ struct xeb_plan_s {
             t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0, t_sort = 0, t_memo = 0;
     size_t memo_bytes = 0;
     std::vector<int> choice;   // per op: CH_AUTO or the autotuner's form
+    std::vector<int64_t> slice_ids;  // seeded subset of slice values (empty: all)
     int n_sms = 152;
     int64_t tables_bytes = 0;
     std::vector<xebk::TrieDesc> trie;
@@ -533,12 +535,12 @@ void slice_candidate(const Network& net, DistinctCounter& dc, const xeb_plan_opt
 std::vector<std::pair<int, Tree>> candidate_trees(const Network& net, DistinctCounter& dc,
                                                   const std::vector<int>& sliced, const xeb_plan_opts& o) {
     std::vector<std::pair<int, Tree>> cands;
-        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_GREEDY) {
+        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_ANNEAL || o.planner == XEB_PLANNER_GREEDY) {
             const int trials = std::max(1, o.greedy_trials);
             for (int t = 0; t < trials; ++t)
                 cands.push_back({XEB_PLANNER_GREEDY, greedy_tree(net, dc, sliced, o.seed + t, t == 0 ? 0.0 : 0.15)});
         }
-        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_SWEEP) {
+        if (o.planner == XEB_PLANNER_AUTO || o.planner == XEB_PLANNER_ANNEAL || o.planner == XEB_PLANNER_SWEEP) {
             std::vector<int> bs, gs;
             if (o.block_qubits > 0) bs = {o.block_qubits};
             else for (int b = 2; b <= 10; ++b) bs.push_back(b);
@@ -651,6 +653,7 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
     }
     Candidate best;
     bool have = false;
+    std::vector<std::pair<double, Tree>> ranked;  // constructed trees by objective
     if (tree) {
         if (!tree->children && tree->n_nodes > 0) return fail(XEB_EINVAL, "tree->children is NULL");
         Tree t(tree->n_nodes);
@@ -664,6 +667,7 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         for (auto& c : cands) {
             Candidate cd_;
             if (!evaluate(p->net, c.second, p->sliced, dc, o, p->elem, k, cd_, err)) continue;
+            ranked.push_back({cd_.f, c.second});
             if (!have || cd_.f < best.f) {
                 best = std::move(cd_);
                 have = true;
@@ -673,6 +677,54 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         if (!have) return fail(XEB_EINVAL, "planner found no valid tree: " + err);
     }
     if (!slices) slice_candidate(p->net, dc, o, p->elem, k, best, p->sliced, err);
+    // App. A local search: always for XEB_PLANNER_ANNEAL; under AUTO when the
+    // constructed trees needed slicing to fit the budget or still do not fit.
+    // Restarts begin from the best constructed trees and from randomised
+    // greedy trees; the best few by the search's own objective are evaluated
+    // exactly (distinct counts, emulated arena) and the best kept.
+    if (!tree && (o.planner == XEB_PLANNER_ANNEAL ||
+                  (o.planner == XEB_PLANNER_AUTO && !slices &&
+                   (!p->sliced.empty() || uint64_t(best.arena_bytes) > o.mem_budget)))) {
+        const int L = int(p->net.leaves.size());
+        const int R = 16;
+        std::sort(ranked.begin(), ranked.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+        std::vector<Tree> starts;
+        for (size_t i = 0; i < ranked.size() && starts.size() < 4; ++i) starts.push_back(ranked[i].second);
+        for (int r = int(starts.size()); r < R; ++r)
+            starts.push_back(greedy_tree(p->net, dc, {}, o.seed + 1000 + uint64_t(r), 0.15));
+        std::vector<std::vector<int>> sls(starts.size(), slices ? p->sliced : std::vector<int>());
+        AnnealOpts ao;
+        ao.steps = o.reserved[5] > 0 ? int64_t(o.reserved[5]) * 1000
+                                     : std::min<int64_t>(int64_t(20) << 20, int64_t(100000) * L);
+        ao.slice_every = slices ? 0 : std::max<int64_t>(1, ao.steps / 400);
+        ao.t0 = 2.0;
+        ao.t1 = 0.001;
+        ao.beta = o.beta;
+        ao.budget_elems = double(std::max<uint64_t>(o.mem_budget, 1)) / double(p->elem);
+        ao.precision = o.precision;
+        ao.elem = p->elem;
+        ao.seed = o.seed;
+        std::vector<AnnealStats> ast;
+        anneal_many(p->net, k, starts, sls, ao, ast);
+        std::vector<size_t> idx(starts.size());
+        for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+        std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+            return ast[x].f_best < ast[y].f_best || (ast[x].f_best == ast[y].f_best && x < y);
+        });
+        bool took = false;
+        for (size_t t = 0; t < std::min<size_t>(3, idx.size()); ++t) {
+            std::vector<int> s = sls[idx[t]];
+            Candidate c;
+            if (!evaluate(p->net, starts[idx[t]], s, dc, o, p->elem, k, c, err)) continue;
+            if (!slices) slice_candidate(p->net, dc, o, p->elem, k, c, s, err);
+            if (c.f < best.f || (o.planner == XEB_PLANNER_ANNEAL && !took)) {
+                best = std::move(c);
+                p->sliced = s;
+                p->planner_used = XEB_PLANNER_ANNEAL;
+                took = true;
+            }
+        }
+    }
     p->tree = best.tree;
     p->an = std::move(best.an);
     p->prog = std::move(best.prog);
@@ -1270,10 +1322,11 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
     double2* acc = reinterpret_cast<double2*>(tables + p->t_acc);
     const int64_t kv_root = an.nodes.back().kv;
     XEB_CUDA(cudaMemsetAsync(acc, 0, size_t(kv_root) * 16, st));
-    const int64_t n_slices = int64_t(1) << p->sliced.size();
+    const int64_t n_run = p->slice_ids.empty() ? int64_t(1) << p->sliced.size() : int64_t(p->slice_ids.size());
     const auto* ldesc = reinterpret_cast<const xebk::LeafDesc*>(tables + p->t_leaf_desc);
     const double es = double(sizeof(T));
-    for (int64_t s = 0; s < n_slices; ++s) {
+    for (int64_t si = 0; si < n_run; ++si) {
+        const int64_t s = p->slice_ids.empty() ? si : p->slice_ids[size_t(si)];
         {
             ProfScope ps(p, st, XEB_KC_LEAVES, 0.0, 0.0);
             XEB_CUDA(xebk::launch_leaves<T>(ldesc, an.L, leafdata, arena, tables, s, st));
@@ -1498,6 +1551,51 @@ extern "C" xeb_status xeb_amplitudes(xeb_plan_s* p, double* out_dev, uintptr_t s
         p->tables_ready = true;
     }
     return s;
+}
+
+extern "C" xeb_status xeb_set_slice_subset(xeb_plan_s* p, double frac, uint64_t seed, int64_t* n_chosen) {
+    if (!p) return fail(XEB_EINVAL, "plan is NULL");
+    if (!(frac > 0)) return fail(XEB_EINVAL, "slice subset fraction must be > 0");
+    const int64_t n = int64_t(1) << p->sliced.size();
+    std::vector<int64_t> ids;
+    if (frac < 1.0) {
+        const int64_t cnt = std::max<int64_t>(1, std::llround(frac * double(n)));
+        if (cnt > (int64_t(1) << 26)) return fail(XEB_EINVAL, "slice subset above 2^26 values");
+        // partial Fisher-Yates over 0..n-1 with the swapped positions kept sparse
+        std::unordered_map<int64_t, int64_t> moved;
+        auto at = [&](int64_t i) {
+            auto it = moved.find(i);
+            return it == moved.end() ? i : it->second;
+        };
+        uint64_t x = seed;
+        for (int64_t j = 0; j < cnt; ++j) {
+            x += 0x9e3779b97f4a7c15ULL;  // splitmix64
+            uint64_t z = x;
+            z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+            z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+            z ^= z >> 31;
+            const int64_t r = j + int64_t(z % uint64_t(n - j));
+            const int64_t vj = at(j), vr = at(r);
+            moved[r] = vj;
+            ids.push_back(vr);
+        }
+    }
+    p->slice_ids = std::move(ids);
+    drop_graph(p, p->graph_plain);
+    for (auto& g : p->graph_prof) drop_graph(p, g);
+    if (n_chosen) *n_chosen = p->slice_ids.empty() ? n : int64_t(p->slice_ids.size());
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_slice_ids(const xeb_plan_s* p, int64_t* ids) {
+    if (!p || !ids) return fail(XEB_EINVAL, "plan or ids is NULL");
+    if (p->slice_ids.empty()) {
+        const int64_t n = int64_t(1) << p->sliced.size();
+        for (int64_t i = 0; i < n; ++i) ids[i] = i;
+    } else {
+        std::copy(p->slice_ids.begin(), p->slice_ids.end(), ids);
+    }
+    return XEB_OK;
 }
 
 extern "C" xeb_status xeb_fidelity(xeb_plan_s* p, double* F, double* m1, double* m2, uintptr_t stream) {

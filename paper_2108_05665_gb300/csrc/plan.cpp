@@ -488,22 +488,35 @@ Costs tree_costs(const Analysis& an, const Program& prog, uint64_t k) {
     return c;
 }
 
-double estimate_time(const Analysis& an, const Program& prog, int precision, size_t elem) {
-    const double bw = 6.6e12 * 0.6;                        // bytes/s reached by streaming kernels
+namespace {
+constexpr double kProfileBw = 6.6e12 * 0.6;  // bytes/s reached by streaming kernels
+}
+
+double contraction_time(double cmac, double bytes, bool tensor_core, int precision) {
     const double simt = precision == XEB_PREC_FP64 ? 0.3e12 : 10.0e12 * 0.5;  // complex MAC/s
     const double tc = 1.0e15 / 3.0 / 8.0 * 0.6;            // 3 TF32 products per complex MAC
+    return std::max(cmac / (tensor_core ? tc : simt), bytes / kProfileBw) + 3e-6;
+}
+
+double expected_distinct(int b, uint64_t k) {
+    if (b <= 0 || k == 0) return 1.0;
+    if (b >= 60) return double(k);
+    const double n = std::ldexp(1.0, b);
+    return n * -std::expm1(double(k) * std::log1p(-1.0 / n));
+}
+
+double estimate_time(const Analysis& an, const Program& prog, int precision, size_t elem) {
     double t = 0;
     for (const Op& op : prog.ops) {
         if (op.kind == OP_PERM) {
-            t += 2.0 * double(op.keys) * std::ldexp(1.0, op.r) * double(elem) / bw + 3e-6;
+            t += 2.0 * double(op.keys) * std::ldexp(1.0, op.r) * double(elem) / kProfileBw + 3e-6;
             continue;
         }
         const double cmac = double(op.kv) * double(op.M) * double(op.N) * double(op.K);
         const double bytes = double(elem) * (double(an.nodes[op.a_node].kv) * std::ldexp(1.0, op.a_rank) +
                                              double(an.nodes[op.b_node].kv) * std::ldexp(1.0, op.b_rank) +
                                              double(op.kv) * double(op.M) * double(op.N));
-        const double rate = (precision == XEB_PREC_TF32X3 && tc_eligible(op)) ? tc : simt;
-        t += std::max(cmac / rate, bytes / bw) + 3e-6;
+        t += contraction_time(cmac, bytes, precision == XEB_PREC_TF32X3 && tc_eligible(op), precision);
     }
     return t;
 }

@@ -135,6 +135,14 @@ inline bool tc_eligible(const Op& op) {
 // read/write counts).
 double estimate_time(const Analysis& an, const Program& prog, int precision, size_t elem);
 
+// The same efficiency profile for one contraction of `cmac` complex MACs that
+// moves `bytes` through HBM, on the tensor cores or the SIMT cores.
+double contraction_time(double cmac, double bytes, bool tensor_core, int precision);
+
+// Expected number of distinct values of b uniform random bits among k draws,
+// 2^b (1 - (1 - 2^-b)^k) (never above the App. C bound min(2^b, k)).
+double expected_distinct(int b, uint64_t k);
+
 // ---- planners ----------------------------------------------------------------
 Tree greedy_tree(const Network& net, DistinctCounter& dc, const std::vector<int>& sliced,
                  uint64_t seed, double noise);
@@ -143,5 +151,40 @@ Tree greedy_tree(const Network& net, DistinctCounter& dc, const std::vector<int>
 // every gate whose predecessors are done, then widens by the earliest ready
 // gate that still fits.
 bool sweep_tree(const Network& net, int block_qubits, int group_leaves, Tree& out, int variant = 0);
+
+// Local search over contraction trees and slice sets (App. A): simulated
+// annealing with the four rewrites (a*b)*c -> (c*b)*a, (a*b)*c -> (a*c)*b,
+// a*(b*c) -> c*(b*a), a*(b*c) -> b*(a*c), whose gain is computed locally
+// (App. C: only the rewritten node and its parent change), and every
+// `slice_every` proposals a slicing move: add the leg with the best memory
+// reduction while over budget, else drop a random sliced leg.  The objective
+// is f = beta max(log2(M / M_max), 0) + |S| + log2 T with T the efficiency-
+// profile time of one slice and M = 2 (sum_v m_v^p)^(1/p), m_v = k_v 2^{r_v}
+// elements of node v (App. C's p-norm estimate of the largest live tensors).
+// During the search k_v is expected_distinct(|B_v|, k).
+struct AnnealOpts {
+    int64_t steps = 0;
+    int64_t slice_every = 0;   // 0: the slice set stays as given
+    double t0 = 0.5, t1 = 0.005;
+    double beta = 10.0;
+    double budget_elems = 1;   // M_max in complex elements
+    double p = 8.0;
+    int precision = XEB_PREC_FP32;
+    size_t elem = 8;
+    uint64_t seed = 1;
+    int max_sliced = 30;
+};
+struct AnnealStats {
+    double f_start = 0, f_best = 0;
+    int64_t accepted = 0;
+};
+// Refines (tree, sliced) in place to the best state visited.
+void anneal_tree(const Network& net, uint64_t k, Tree& tree, std::vector<int>& sliced, const AnnealOpts& ao,
+                 AnnealStats* stats = nullptr);
+// Independent restarts, one per start tree (seed derived from ao.seed and the
+// restart index, so the result does not depend on the number of host threads
+// that run them); each tree and slice set is refined in place.
+void anneal_many(const Network& net, uint64_t k, std::vector<Tree>& trees, std::vector<std::vector<int>>& sliced,
+                 const AnnealOpts& ao, std::vector<AnnealStats>& stats);
 
 }  // namespace xebp

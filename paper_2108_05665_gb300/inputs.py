@@ -219,4 +219,11 @@ WORKLOADS = {
     # 5x8 grid, 12 cycles, 100,000 uniform bitstrings (sliced).
     "grid5x8_m12_k100000": Workload("grid5x8_m12_k100000", 5, 8, 12, 100000,
                                     1003, 2003),
+    # 6x9 grid without its (0, 0) corner (53 qubits), 12 cycles, 300,000
+    # uniform bitstrings (sliced; timed on a seeded subset of the slices).
+    "grid6x9m1_m12_k300000": Workload("grid6x9m1_m12_k300000", 6, 9, 12, 300000,
+                                      1004, 2004, missing=((0, 0),)),
+    # the same grid, 14 cycles, 1,000,000 uniform bitstrings.
+    "grid6x9m1_m14_k1000000": Workload("grid6x9m1_m14_k1000000", 6, 9, 14, 1000000,
+                                       1005, 2005, missing=((0, 0),)),
 }

@@ -51,7 +51,7 @@ def test_network_convention_matches_oracle():
         assert B.xeb_network_info(circ) == (len(net.leaves), net.n_legs)
 
 
-@pytest.mark.parametrize("planner", [B.XEB_PLANNER_GREEDY, B.XEB_PLANNER_SWEEP, None])
+@pytest.mark.parametrize("planner", [B.XEB_PLANNER_GREEDY, B.XEB_PLANNER_SWEEP, B.XEB_PLANNER_ANNEAL, None])
 def test_plan_counts_and_costs_match_oracle(planner):
     w = inputs.WORKLOADS["grid3x4_m8_k1000"]
     circ = w.circuit()
@@ -121,3 +121,64 @@ def test_invalid_inputs_rejected():
     bad_c = inputs.Circuit(6, [inputs.Gate(2, (0, 0), inputs.FSIM)])
     with pytest.raises(B.XebError):
         B.xeb_network_info(bad_c)
+
+
+def test_anneal_fits_budget_and_keeps_exact_counts():
+    """The local search of App. A under a budget 1/16 of the unsliced arena:
+    the plan fits, slices some legs, its counts and costs still agree with
+    the oracle's memo semantics, and AUTO (which runs the search when slicing
+    is needed and keeps it only if better) is never worse than either
+    constructed family alone."""
+    circ = inputs.random_grid_circuit(4, 5, 12, 4242)
+    bs = inputs.uniform_bitstrings(20, 700, 4343)
+    net = network.fused_network(circ)
+    o = B.xeb_default_opts()
+    o.precision = B.XEB_PREC_TF32X3
+    p0 = B.xeb_plan_create(circ, bs, opts=o)
+    full = B.xeb_plan_stats(p0)
+    B.xeb_plan_destroy(p0)
+    o.mem_budget = full["arena_bytes"] // 16
+    objs = {}
+    for planner in (B.XEB_PLANNER_ANNEAL, B.XEB_PLANNER_AUTO, B.XEB_PLANNER_GREEDY, B.XEB_PLANNER_SWEEP):
+        o.planner = planner
+        p = B.xeb_plan_create(circ, bs, opts=o)
+        try:
+            st = B.xeb_plan_stats(p)
+            objs[planner] = st["objective"]
+            if planner == B.XEB_PLANNER_ANNEAL:
+                assert st["planner_used"] == B.XEB_PLANNER_ANNEAL
+                assert st["arena_bytes"] <= o.mem_budget
+                assert st["n_sliced"] >= 1
+                tree, sliced = B.xeb_plan_tree(p)
+                memo.check_tree(tree, len(net.leaves))
+                kt = memo.key_tables(net, tree, bs)
+                c, rw = memo.costs(net, tree, kt["k"], sliced)
+                assert st["flops_per_slice"] == 8 * c
+                assert st["rw_elems_per_slice"] == rw
+        finally:
+            B.xeb_plan_destroy(p)
+    assert objs[B.XEB_PLANNER_AUTO] <= min(objs[B.XEB_PLANNER_GREEDY], objs[B.XEB_PLANNER_SWEEP]) + 1e-12
+
+
+def test_slice_subset_is_seeded_and_distinct():
+    circ = inputs.random_grid_circuit(3, 4, 8, 11)
+    bs = inputs.uniform_bitstrings(12, 50, 12)
+    net = network.fused_network(circ)
+    bonds = sorted({l for leaf in net.leaves for l in leaf.legs})
+    p = B.xeb_plan_create(circ, bs, slices=bonds[:6])
+    try:
+        assert B.xeb_set_slice_subset(p, 1.0, 0) == 64
+        assert list(B.xeb_plan_slice_ids(p, 64)) == list(range(64))
+        n = B.xeb_set_slice_subset(p, 0.25, 99)
+        assert n == 16
+        ids = B.xeb_plan_slice_ids(p, n)
+        assert len(set(ids.tolist())) == 16 and ids.min() >= 0 and ids.max() < 64
+        B.xeb_set_slice_subset(p, 0.25, 99)
+        assert np.array_equal(B.xeb_plan_slice_ids(p, n), ids)       # same seed, same subset
+        B.xeb_set_slice_subset(p, 0.25, 100)
+        assert not np.array_equal(B.xeb_plan_slice_ids(p, n), ids)
+        assert B.xeb_set_slice_subset(p, 1e-9, 1) == 1                # at least one value
+        with pytest.raises(B.XebError):
+            B.xeb_set_slice_subset(p, 0.0, 1)
+    finally:
+        B.xeb_plan_destroy(p)
