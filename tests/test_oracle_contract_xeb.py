@@ -68,3 +68,34 @@ def test_grid5x6_fixture_consistent():
     uni = z["bitstrings"][5000:]
     w = inputs.WORKLOADS["grid5x6_m14_k10000"]
     assert np.array_equal(uni, inputs.uniform_bitstrings(n, 5000, w.bitstring_seed))
+
+
+def test_sequence_cost_by_hand():
+    # A(l0,l1) * B(l1,l2): 2^3 multiplications, result (l0,l2); then * C(l2): 2^2
+    assert contract.sequence_cost([[0, 1], [1, 2], [2]], [(0, 1), (0, 1)]) == 8 + 4
+    # a worse order: B * C first (2^2), then A * (B C): legs l0, l1 -> 2^2
+    assert contract.sequence_cost([[0, 1], [1, 2], [2]], [(1, 2), (0, 1)]) == 4 + 4
+
+
+def test_search_order_same_amplitudes_fewer_multiplications():
+    circ = inputs.random_grid_circuit(3, 4, 10, 808)
+    net = network.fused_network(circ)
+    bits = inputs.uniform_bitstrings(12, 6, 809)
+    legsets = [legs for _, legs in (network.project_leaf(l, 0) for l in net.leaves)]
+    seq = contract.search_order(legsets, trials=24, seed=3)
+    assert contract.sequence_cost(legsets, seq) <= contract.sequence_cost(legsets, contract.greedy_order(legsets))
+    ref = statevec.amplitudes(circ, bits)
+    assert np.abs(contract.amplitudes(net, bits, seq=seq) - ref).max() < 1e-12
+
+
+def test_slice_value_subsets_partition_the_sum():
+    circ = inputs.random_grid_circuit(3, 3, 6, 606)
+    net = network.fused_network(circ)
+    bits = inputs.uniform_bitstrings(9, 5, 607)
+    bonds = sorted({l for leaf in net.leaves for l in leaf.legs})
+    sliced = [bonds[2], bonds[9], bonds[20]]
+    part = contract.amplitudes(net, bits, sliced, values=[0, 3, 5])
+    rest = contract.amplitudes(net, bits, sliced, values=[1, 2, 4, 6, 7])
+    ref = statevec.amplitudes(circ, bits)
+    assert np.abs(part + rest - ref).max() < 1e-12
+    assert np.abs(part - ref).max() > 1e-6          # a subset alone is not the amplitude
