@@ -210,9 +210,10 @@ def main():
                     help="launch the step kernel by kernel instead of replaying one captured CUDA graph")
     ap.add_argument("--tc-variant", default="tmem", choices=["tmem", "smem"],
                     help="tensor-core kernel: B^T in tensor memory (default) or split B in shared memory")
-    ap.add_argument("--planner", default="plain", choices=["plain", "learned"],
+    ap.add_argument("--planner", default="plain", choices=["plain", "learned", "anneal"],
                     help="plain: the planner's own objective; learned: the cost model's top candidates and the "
-                         "plain plan are timed and the fastest kept (plan-time, outside the timed region)")
+                         "plain plan are timed and the fastest kept (plan-time, outside the timed region); "
+                         "anneal: the App. A local search refines the constructed trees")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time every kernel form of every contraction this many times and keep the fastest "
                          "(plan-time, outside the timed region; 0 = off)")
@@ -246,6 +247,8 @@ def main():
     o.reserved[1] = 1 if args.tc_variant == "smem" else 0
     o.reserved[2] = 1 if args.eager else 0
     o.reserved[3] = 1 if args.tc_loads == "gather" else 0
+    if args.planner == "anneal":
+        o.planner = B.XEB_PLANNER_ANNEAL
     big = w.n_qubits > 30
     if args.mem_gb is not None:
         o.mem_budget = int(args.mem_gb * 2 ** 30)

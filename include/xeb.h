@@ -255,6 +255,7 @@ enum {
     XEB_KC_GEMM_TC = 9,       /* a4 tcgen05 split-precision complex GEMM         */
     XEB_KC_GEMM_STREAM = 10,  /* a4 memory-bound streaming contraction (SIMT)    */
     XEB_KC_GEMM_MEMO = 11,    /* a4 memo-trie levels: keys grouped by left key   */
+    XEB_KC_GEMM_KDEEP = 12,   /* a4 keyed contractions with a deep summed index  */
     XEB_N_KC = 16
 };
 
@@ -268,6 +269,14 @@ xeb_status xeb_plan_profile(struct xeb_plan_s* plan, int enable);
  * algorithmic bytes (each operand tensor read once, each result written
  * once).  Each output is a host array of XEB_N_KC doubles (may be NULL).
  * Synchronises on the recorded events. */
+/* Per contraction of the plan's program (in program order): accumulated
+ * device milliseconds and launches since profiling was enabled, its kernel
+ * class (XEB_KC_*, -1 before xeb_plan_bind) and its shape (M, N, K, k_v as
+ * doubles, [n][4]).  Writes min(cap, n) entries of each non-NULL host array;
+ * *n_ops receives n.  Synchronises on the recorded events. */
+xeb_status xeb_plan_profile_ops(struct xeb_plan_s* plan, int cap, double* ms, double* launches, int32_t* cls,
+                                double* shape, int32_t* n_ops);
+
 xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* launches, double* flops,
                                  double* bytes);
 

@@ -117,6 +117,8 @@ _PROTOS = {
     "xeb_set_slice_subset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64,
                                             ctypes.POINTER(ctypes.c_int64)]),
     "xeb_plan_slice_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
+                                            ctypes.POINTER(ctypes.c_int32)]),
     "xeb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -250,6 +252,23 @@ def xeb_amplitudes(plan, out_dev_ptr: int, stream: int):
     _check(load().xeb_amplitudes(plan, ctypes.c_void_p(out_dev_ptr or None), ctypes.c_void_p(stream or None)))
 
 
+def xeb_plan_profile_ops(plan):
+    """Per contraction: ms, launches, kernel class name, (M, N, K, kv)."""
+    n = ctypes.c_int32()
+    _check(load().xeb_plan_profile_ops(plan, 0, None, None, None, None, ctypes.byref(n)))
+    cnt = n.value
+    ms = np.zeros(cnt)
+    la = np.zeros(cnt)
+    cls = np.zeros(cnt, dtype=np.int32)
+    shp = np.zeros((cnt, 4))
+    _check(load().xeb_plan_profile_ops(plan, cnt, ms.ctypes.data_as(_dblp), la.ctypes.data_as(_dblp),
+                                       cls.ctypes.data_as(_i32p), shp.ctypes.data_as(_dblp), ctypes.byref(n)))
+    return [{"ms": float(ms[i]), "launches": int(la[i]),
+             "kernel": KERNEL_CLASSES[cls[i]] if 0 <= cls[i] < len(KERNEL_CLASSES) else None,
+             "M": int(shp[i, 0]), "N": int(shp[i, 1]), "K": int(shp[i, 2]), "kv": int(shp[i, 3])}
+            for i in range(cnt)]
+
+
 def xeb_set_slice_subset(plan, frac: float, seed: int) -> int:
     """Run only a seeded subset of the slice values (partial sums); returns its size."""
     n = ctypes.c_int64()
@@ -292,7 +311,7 @@ def xeb_linear_xeb_noalloc(amps_dev_ptr: int, k: int, n_qubits: int, out_dev_ptr
 
 
 KERNEL_CLASSES = ["trie", "leaves", "permute", "gemm_tiled", "gemm_gemv", "gemm_tail", "gemm_generic",
-                  "accum", "xeb", "gemm_tc", "gemm_stream", "gemm_memo"]
+                  "accum", "xeb", "gemm_tc", "gemm_stream", "gemm_memo", "gemm_kdeep"]
 XEB_N_KC = 16
 
 

@@ -311,6 +311,7 @@ struct xeb_plan_s {
         int cls;
         cudaEvent_t a, b;
         double flops, bytes;
+        int op;  // program op index, -1 for non-contraction kernels
     };
     std::vector<Rec> pending;
     // A whole step (key tables + every slice + XEB) as one CUDA graph,
@@ -330,6 +331,7 @@ struct xeb_plan_s {
     bool capturing_prof = false;
     std::vector<cudaEvent_t> event_pool;
     double prof_ms[XEB_N_KC] = {0}, prof_n[XEB_N_KC] = {0}, prof_flops[XEB_N_KC] = {0}, prof_bytes[XEB_N_KC] = {0};
+    std::vector<double> op_ms, op_n;  // per program op
 };
 
 namespace {
@@ -350,9 +352,10 @@ struct ProfScope {
     cudaStream_t st;
     int cls;
     double flops, bytes;
+    int op;
     cudaEvent_t a = nullptr;
-    ProfScope(xeb_plan_s* p_, cudaStream_t st_, int cls_, double flops_, double bytes_)
-        : p(p_), st(st_), cls(cls_), flops(flops_), bytes(bytes_) {
+    ProfScope(xeb_plan_s* p_, cudaStream_t st_, int cls_, double flops_, double bytes_, int op_ = -1)
+        : p(p_), st(st_), cls(cls_), flops(flops_), bytes(bytes_), op(op_) {
         if (p->profiling) {
             a = take_event(p);
             record(a);
@@ -369,7 +372,7 @@ struct ProfScope {
         if (!p->profiling || !a) return;
         cudaEvent_t b = take_event(p);
         record(b);
-        p->pending.push_back({cls, a, b, flops, bytes});
+        p->pending.push_back({cls, a, b, flops, bytes, op});
     }
 };
 
@@ -381,6 +384,14 @@ void accumulate(xeb_plan_s* p, const std::vector<xeb_plan_s::Rec>& recs) {
             p->prof_n[r.cls] += 1;
             p->prof_flops[r.cls] += r.flops;
             p->prof_bytes[r.cls] += r.bytes;
+            if (r.op >= 0) {
+                if (p->op_ms.size() <= size_t(r.op)) {
+                    p->op_ms.resize(size_t(r.op) + 1, 0.0);
+                    p->op_n.resize(size_t(r.op) + 1, 0.0);
+                }
+                p->op_ms[size_t(r.op)] += ms;
+                p->op_n[size_t(r.op)] += 1;
+            }
         }
     }
 }
@@ -462,9 +473,12 @@ struct Candidate {
 };
 
 bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& sliced, DistinctCounter& dc,
-              const xeb_plan_opts& o, size_t elem, uint64_t k, Candidate& cand, std::string& err) {
+              const xeb_plan_opts& o, size_t elem, uint64_t k, Candidate& cand, std::string& err,
+              bool orient = true) {
     cand.tree = tree;
-    if (!analyze(net, tree, sliced, cand.an, err)) return false;
+    if (orient && check_tree(tree, int(net.leaves.size()), err)) orient_tree(net, cand.tree, sliced);
+    const Tree& tree_ = cand.tree;
+    if (!analyze(net, tree_, sliced, cand.an, err)) return false;
     fill_counts(cand.an, dc);
     build_program(cand.an, cand.prog, o.reserved[0] == 0,
                   o.precision == XEB_PREC_TF32X3 && o.reserved[1] != 1);
@@ -489,7 +503,7 @@ bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& slic
 // time over all slices); ties go to the smaller arena, then the smaller
 // largest tensor, then the smaller total tensor size.
 void slice_candidate(const Network& net, DistinctCounter& dc, const xeb_plan_opts& o, size_t elem, uint64_t k,
-                     Candidate& best, std::vector<int>& sliced, std::string& err) {
+                     Candidate& best, std::vector<int>& sliced, std::string& err, bool orient = true) {
         auto node_elems = [](const Analysis& an, int v) {
             return double(an.nodes[v].kv) * std::ldexp(1.0, int(an.nodes[v].legs.size()));
         };
@@ -516,7 +530,7 @@ void slice_candidate(const Network& net, DistinctCounter& dc, const xeb_plan_opt
                 std::vector<int> s2 = sliced;
                 s2.push_back(l);
                 Candidate c;
-                if (!evaluate(net, best.tree, s2, dc, o, elem, k, c, err)) continue;
+                if (!evaluate(net, best.tree, s2, dc, o, elem, k, c, err, orient)) continue;
                 const auto m = measure(c);
                 if (bl < 0 || m < bm) {
                     bc = std::move(c);
@@ -658,7 +672,7 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         if (!tree->children && tree->n_nodes > 0) return fail(XEB_EINVAL, "tree->children is NULL");
         Tree t(tree->n_nodes);
         for (int i = 0; i < tree->n_nodes; ++i) t[i] = {tree->children[2 * i], tree->children[2 * i + 1]};
-        if (!evaluate(p->net, t, p->sliced, dc, o, p->elem, k, best, err)) return fail(XEB_EINVAL, err);
+        if (!evaluate(p->net, t, p->sliced, dc, o, p->elem, k, best, err, false)) return fail(XEB_EINVAL, err);
         have = true;
         p->planner_used = 0;
     } else {
@@ -676,7 +690,7 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         }
         if (!have) return fail(XEB_EINVAL, "planner found no valid tree: " + err);
     }
-    if (!slices) slice_candidate(p->net, dc, o, p->elem, k, best, p->sliced, err);
+    if (!slices) slice_candidate(p->net, dc, o, p->elem, k, best, p->sliced, err, tree == nullptr);
     // App. A local search: always for XEB_PLANNER_ANNEAL; under AUTO when the
     // constructed trees needed slicing to fit the budget or still do not fit.
     // Restarts begin from the best constructed trees and from randomised
@@ -1006,6 +1020,7 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
     if (stream_tile(op, p->elem, g.s))
         g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
     else if (op.N == 1) g.kernel = xebk::GK_GEMV;
+    else if (op.K >= 32 && std::min(op.M, op.N) <= xebk::kKdTile && d.c_natural) g.kernel = xebk::GK_KDEEP;
     else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;
     else g.kernel = xebk::GK_GENERIC;
     return true;
@@ -1343,9 +1358,10 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
                 const double by = es * (ka * double(op.M * op.K) + kb * double(op.K * op.N) +
                                         double(op.kv) * double(op.M * op.N));
-                static const int cls_of[6] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
-                                              XEB_KC_GEMM_TAIL, XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO};
-                ProfScope ps(p, st, g.kernel >= GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by);
+                static const int cls_of[7] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
+                                              XEB_KC_GEMM_TAIL,    XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO,
+                                              XEB_KC_GEMM_KDEEP};
+                ProfScope ps(p, st, g.kernel >= GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by, int(i));
                 XEB_CUDA(launch_gemm_op<T>(p, g, arena, tables, st));
             }
         }
@@ -1733,7 +1749,40 @@ extern "C" xeb_status xeb_plan_profile(xeb_plan_s* p, int enable) {
     if (!p) return fail(XEB_EINVAL, "NULL plan");
     drain_profile(p);
     for (int c = 0; c < XEB_N_KC; ++c) p->prof_ms[c] = p->prof_n[c] = p->prof_flops[c] = p->prof_bytes[c] = 0;
+    p->op_ms.clear();
+    p->op_n.clear();
     p->profiling = enable != 0;
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_profile_ops(xeb_plan_s* p, int cap, double* ms, double* launches, int32_t* cls,
+                                           double* shape, int32_t* n_ops) {
+    if (!p || !n_ops) return fail(XEB_EINVAL, "NULL plan or n_ops");
+    drain_profile(p);
+    const Program& pr = p->prog;
+    static const int cls_of[7] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV, XEB_KC_GEMM_TAIL,
+                                  XEB_KC_GEMM_STREAM,  XEB_KC_GEMM_MEMO,  XEB_KC_GEMM_KDEEP};
+    const int n = int(pr.ops.size());
+    *n_ops = n;
+    for (int i = 0; i < std::min(n, cap); ++i) {
+        const Op& op = pr.ops[size_t(i)];
+        if (ms) ms[i] = size_t(i) < p->op_ms.size() ? p->op_ms[size_t(i)] : 0.0;
+        if (launches) launches[i] = size_t(i) < p->op_n.size() ? p->op_n[size_t(i)] : 0.0;
+        if (cls) {
+            if (op.kind == OP_PERM) cls[i] = XEB_KC_PERMUTE;
+            else if (!p->bound || p->gemms.size() <= size_t(i)) cls[i] = -1;
+            else {
+                const int kk = p->gemms[size_t(i)].kernel;
+                cls[i] = kk >= GK_TC ? XEB_KC_GEMM_TC : cls_of[kk];
+            }
+        }
+        if (shape) {
+            shape[4 * i + 0] = double(op.M);
+            shape[4 * i + 1] = double(op.N);
+            shape[4 * i + 2] = double(op.K);
+            shape[4 * i + 3] = double(op.kv);
+        }
+    }
     return XEB_OK;
 }
 

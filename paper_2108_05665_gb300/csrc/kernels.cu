@@ -539,6 +539,146 @@ __global__ void __launch_bounds__(256) k_gemm_tiled(const __grid_constant__ Gemm
     }
 }
 
+// Keyed contractions with a deep summed index and a narrow result (for every
+// key u a tile of at most 32 x 32 outputs over K >= 32 summed elements, e.g.
+// the near-root nodes of sliced plans).  A CTA takes one (key, 32-row,
+// 32-column) tile; every step stages a 64-deep chunk of A and B in shared
+// memory (the next chunk is loaded into registers while this one is used),
+// each of the 8 warps sums 8 of its columns of k into a full 32 x 32 partial
+// tile (lane: 4 rows x 8 columns), and the warps' partial tiles are added in
+// shared memory in three halving rounds before warp 0 writes the tile.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_gemm_kdeep(const __grid_constant__ GemmDesc g, T* __restrict__ arena,
+                                                       int64_t mt, int64_t nt) {
+    extern __shared__ __align__(16) unsigned char kd_smem[];
+    T* As = reinterpret_cast<T*>(kd_smem);                 // [kKdChunk][32]
+    T* Bs = As + kKdChunk * kKdTile;                       // [kKdChunk][32]
+    int64_t* rowA = reinterpret_cast<int64_t*>(Bs + kKdChunk * kKdTile);
+    int64_t* colB = rowA + kKdTile;
+    int64_t* kA = colB + kKdTile;                          // [2][kKdChunk] (double-buffered)
+    int64_t* kB = kA + 2 * kKdChunk;
+    T* red = As;                                           // [4][32 * 32] after the last chunk
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rg = lane >> 2, cg = lane & 3;               // rows 4 rg .. 4 rg + 3, columns 8 cg .. 8 cg + 7
+    const bool a_along_k = g.nak > 0 && g.apk[0] == 0;
+    const bool b_along_n = g.nbn > 0 && g.bpn[0] == 0;
+    const int64_t n_tiles = g.kv * mt * nt;
+    const int64_t n_chunks = (g.K + kKdChunk - 1) / kKdChunk;
+    constexpr int kPer = kKdChunk * kKdTile / 256;         // staged elements per thread per operand
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t u = tile % g.kv;
+        const int64_t rest = tile / g.kv;
+        const int64_t m0 = (rest % mt) * kKdTile;
+        const int64_t n0 = (rest / mt) * kKdTile;
+        const T* A = arena + g.a_off + (g.uL ? int64_t(g.uL[u]) : 0) * g.a_key;
+        const T* B = arena + g.b_off + (g.uR ? int64_t(g.uR[u]) : 0) * g.b_key;
+        if (tid < kKdTile) rowA[tid] = m0 + tid < g.M ? scatter(m0 + tid, g.apm, g.nam) : -1;
+        else if (tid < 2 * kKdTile) colB[tid - kKdTile] = n0 + tid - kKdTile < g.N ? scatter(n0 + tid - kKdTile, g.bpn, g.nbn) : -1;
+        auto k_offsets = [&](int64_t c, int buf) {
+            if (tid < kKdChunk) {
+                const int64_t k = c * kKdChunk + tid;
+                kA[buf * kKdChunk + tid] = k < g.K ? scatter(k, g.apk, g.nak) : -1;
+            } else if (tid < 2 * kKdChunk) {
+                const int64_t k = c * kKdChunk + tid - kKdChunk;
+                kB[buf * kKdChunk + tid - kKdChunk] = k < g.K ? scatter(k, g.bpk, g.nbk) : -1;
+            }
+        };
+        // element e of a chunk: (row or column index, k) with the operand's
+        // lowest address dimension fastest across threads
+        auto a_idx = [&](int e, int& mm, int& kk) {
+            if (a_along_k) { kk = e % kKdChunk; mm = e / kKdChunk; } else { mm = e % kKdTile; kk = e / kKdTile; }
+        };
+        auto b_idx = [&](int e, int& nn, int& kk) {
+            if (b_along_n) { nn = e % kKdTile; kk = e / kKdTile; } else { kk = e % kKdChunk; nn = e / kKdChunk; }
+        };
+        T ra[kPer], rb[kPer];
+        auto load = [&](int buf) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                int mm, kk, nn, kb;
+                a_idx(tid + j * 256, mm, kk);
+                const int64_t ka = kA[buf * kKdChunk + kk];
+                ra[j] = (rowA[mm] >= 0 && ka >= 0) ? A[rowA[mm] + ka] : czero<T>();
+                b_idx(tid + j * 256, nn, kb);
+                const int64_t kbo = kB[buf * kKdChunk + kb];
+                rb[j] = (colB[nn] >= 0 && kbo >= 0) ? B[kbo + colB[nn]] : czero<T>();
+            }
+        };
+        k_offsets(0, 0);
+        __syncthreads();
+        load(0);
+        T acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = czero<T>();
+        for (int64_t c = 0; c < n_chunks; ++c) {
+            const int buf = int(c & 1);
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                int mm, kk, nn, kb;
+                a_idx(tid + j * 256, mm, kk);
+                As[kk * kKdTile + mm] = ra[j];
+                b_idx(tid + j * 256, nn, kb);
+                Bs[kb * kKdTile + nn] = rb[j];
+            }
+            if (c + 1 < n_chunks) k_offsets(c + 1, buf ^ 1);
+            __syncthreads();
+            if (c + 1 < n_chunks) load(buf ^ 1);   // next chunk in flight during the sums
+#pragma unroll
+            for (int kk = warp * (kKdChunk / 8); kk < (warp + 1) * (kKdChunk / 8); ++kk) {
+                T af[4], bf[8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) af[i] = As[kk * kKdTile + rg * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) bf[j] = Bs[kk * kKdTile + cg * 8 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = cfma(acc[i][j], af[i], bf[j]);
+            }
+            __syncthreads();
+        }
+        // sum the 8 warps' partial tiles: 8 -> 4 -> 2 -> 1
+#pragma unroll
+        for (int half = 4; half >= 1; half >>= 1) {
+            if (warp >= half && warp < 2 * half) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) red[(warp - half) * 1024 + (rg * 4 + i) * 32 + cg * 8 + j] = acc[i][j];
+            }
+            __syncthreads();
+            if (warp < half) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = cadd(acc[i][j], red[warp * 1024 + (rg * 4 + i) * 32 + cg * 8 + j]);
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+            T* C = arena + g.c_off + u * g.c_key;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t m = m0 + rg * 4 + i;
+                if (m >= g.M) continue;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int64_t n = n0 + cg * 8 + j;
+                    if (n < g.N) C[m * g.N + n] = acc[i][j];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+constexpr size_t kdeep_smem_bytes() {
+    return size_t(2 * kKdChunk * kKdTile) * sizeof(T) + size_t(2 * kKdTile + 4 * kKdChunk) * sizeof(int64_t);
+}
+
 // N == 1: one thread per (left-key group, row m); the A row is shared by all
 // keys of the group (keys are sorted by their left key, so groups are runs).
 constexpr int kGemvK = 256;
@@ -607,6 +747,11 @@ cudaError_t launch_gemm(int kernel, const GemmDesc& g, T* arena, cudaStream_t st
         case GK_GEMV:
             k_gemm_gemv<T><<<grid_for(g.n_groups * g.M, 256, cap), 256, 0, st>>>(g, arena);
             break;
+        case GK_KDEEP: {
+            const int64_t mt = (g.M + kKdTile - 1) / kKdTile, nt = (g.N + kKdTile - 1) / kKdTile;
+            k_gemm_kdeep<T><<<grid_for(g.kv * mt * nt, 1, 152 * 2), 256, kdeep_smem_bytes<T>(), st>>>(g, arena, mt, nt);
+            break;
+        }
         case GK_TAIL:
             k_gemm_tail<T><<<grid_for(g.kv * 32, 256, cap), 256, 0, st>>>(g, arena);
             break;
@@ -1137,6 +1282,9 @@ cudaError_t prepare_kernels() {
     XEB_PREP_STREAM(double2, 1) XEB_PREP_STREAM(double2, 2) XEB_PREP_STREAM(double2, 4)
     XEB_PREP_STREAM(double2, 8) XEB_PREP_STREAM(double2, 16)
 #undef XEB_PREP_STREAM
+    e = cudaFuncSetAttribute(k_gemm_kdeep<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(kdeep_smem_bytes<double2>()));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_gemm_memo<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_gemm_memo<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);

@@ -80,7 +80,9 @@ struct StreamDesc {
     int8_t pos[32];
 };
 
-enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4, GK_MEMO = 5 };
+enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4, GK_MEMO = 5, GK_KDEEP = 6 };
+constexpr int kKdTile = 32;   // deep-K contractions: 32 x 32 result tile per CTA
+constexpr int kKdChunk = 64;  // summed-index chunk staged per step (8 per warp)
 constexpr int kStreamMaxK = 64, kStreamMaxN = 64;
 constexpr int kStreamEPT = 8;   // A-tile elements per thread
 constexpr int kStreamStages = 4;  // A tiles in flight per CTA

@@ -252,6 +252,29 @@ bool analyze(const Network& net, const Tree& tree, const std::vector<int>& slice
     return true;
 }
 
+void orient_tree(const Network& net, Tree& t, const std::vector<int>& sliced) {
+    const int L = int(net.leaves.size());
+    std::set<int> sl(sliced.begin(), sliced.end());
+    std::vector<std::vector<int>> legs(t.size());  // internal node legs, sorted
+    auto legs_of = [&](int ref) -> std::vector<int> {
+        if (ref >= 0) return legs[ref];
+        std::vector<int> v;
+        for (int l : net.leaves[-1 - ref].legs)
+            if (!sl.count(l)) v.push_back(l);
+        std::sort(v.begin(), v.end());
+        return v;
+    };
+    (void)L;
+    for (size_t i = 0; i < t.size(); ++i) {
+        const std::vector<int> a = legs_of(t[i][0]), b = legs_of(t[i][1]);
+        std::vector<int> shared, x;
+        std::set_intersection(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(shared));
+        std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(x));
+        legs[i] = x;
+        if (b.size() > a.size()) std::swap(t[i][0], t[i][1]);
+    }
+}
+
 int64_t DistinctCounter::count(uint64_t mask) {
     if (mask == 0 || k == 0) return 1;
     auto it = cache.find(mask);

@@ -63,6 +63,11 @@ struct DistinctCounter {
 };
 
 bool check_tree(const Tree& t, int n_leaves, std::string& err);
+// Commutativity (App. A): put the child with more free (unshared, unsliced)
+// legs on the left of every node, so each contraction has M >= N (the left
+// child is the A operand).  Costs are unchanged; only the in-order bit order
+// and the operand roles change.
+void orient_tree(const Network& net, Tree& t, const std::vector<int>& sliced);
 bool analyze(const Network& net, const Tree& tree, const std::vector<int>& sliced,
              Analysis& an, std::string& err);
 void fill_counts(Analysis& an, DistinctCounter& dc);
