@@ -277,6 +277,17 @@ xeb_status xeb_plan_profile(struct xeb_plan_s* plan, int enable);
 xeb_status xeb_plan_profile_ops(struct xeb_plan_s* plan, int cap, double* ms, double* launches, int32_t* cls,
                                 double* shape, int32_t* n_ops);
 
+/* Operand and result addressing of step `op_index` of the plan's contraction
+ * program (host only; the program of App. A/C's tree, one step per
+ * contraction or permutation).  Writes min(cap, n) int32 values to out (may be
+ * NULL) and n to *n_out: kind (1 permute, 2 contraction), node, A node, B
+ * node, then the lengths of the six lists a_pos_m, a_pos_k, b_pos_k, b_pos_n,
+ * c_pos_m, c_pos_n, then the lists themselves.  Entry i of a list is the
+ * address bit (legs have dimension 2) of bit i of the row (m), summed (k) or
+ * column (n) index in operand A, B or the result C.  XEB_EINVAL for a NULL
+ * plan or n_out, or an index outside the program. */
+xeb_status xeb_plan_op_layout(const struct xeb_plan_s* plan, int op_index, int32_t* out, int cap, int32_t* n_out);
+
 xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* launches, double* flops,
                                  double* bytes);
 

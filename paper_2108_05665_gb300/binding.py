@@ -117,6 +117,7 @@ _PROTOS = {
     "xeb_set_slice_subset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64,
                                             ctypes.POINTER(ctypes.c_int64)]),
     "xeb_plan_slice_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "xeb_plan_op_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, ctypes.c_int, _i32p]),
     "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "xeb_last_error": (ctypes.c_char_p, []),
@@ -267,6 +268,23 @@ def xeb_plan_profile_ops(plan):
              "kernel": KERNEL_CLASSES[cls[i]] if 0 <= cls[i] < len(KERNEL_CLASSES) else None,
              "M": int(shp[i, 0]), "N": int(shp[i, 1]), "K": int(shp[i, 2]), "kv": int(shp[i, 3])}
             for i in range(cnt)]
+
+
+def xeb_plan_op_layout(plan, op_index: int):
+    """Addressing of one program step: kind, node, A/B nodes and the address
+    bit lists a_pos_m, a_pos_k, b_pos_k, b_pos_n, c_pos_m, c_pos_n."""
+    n = ctypes.c_int32()
+    _check(load().xeb_plan_op_layout(plan, op_index, None, 0, ctypes.byref(n)))
+    v = np.zeros(n.value, dtype=np.int32)
+    _check(load().xeb_plan_op_layout(plan, op_index, _ptr(v, ctypes.c_int32), n.value, ctypes.byref(n)))
+    v = [int(x) for x in v]
+    lens = v[4:10]
+    out = {"kind": v[0], "node": v[1], "a_node": v[2], "b_node": v[3]}
+    pos = 10
+    for name, ln in zip(("a_pos_m", "a_pos_k", "b_pos_k", "b_pos_n", "c_pos_m", "c_pos_n"), lens):
+        out[name] = v[pos:pos + ln]
+        pos += ln
+    return out
 
 
 def xeb_set_slice_subset(plan, frac: float, seed: int) -> int:

@@ -124,6 +124,26 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits, bool tmem_variant) {
         t.st_idx[i] = int8_t(st[i][2]);
         if (st[i][1]) t.st_is_n |= 1u << i;
     }
+    // Staging swizzle: the epilogue reads the tile with lane bit i = tile bit
+    // i (i < 5) of ascending C order, 8 bytes per lane; the bank pair of slot
+    // row * 64 + n' is n' mod 16.  Column bits j < 4 move it by 2^j; row bits
+    // and column bits >= 4 do not, so each of those lane bits gets an unused
+    // unit vector of GF(2)^4: the 16 lanes of a half-warp then read 16
+    // distinct bank pairs (no conflicts) whatever the result layout.
+    std::memset(t.st_swz, 0, sizeof(t.st_swz));
+    if (tmem_variant) {
+        unsigned used = 0;
+        for (int i = 0; i < 4 && i < t.Tst; ++i)
+            if (st[i][1] && st[i][2] < 4) used |= 1u << st[i][2];
+        for (int i = 0; i < 4 && i < t.Tst; ++i) {
+            if (st[i][1] && st[i][2] < 4) continue;
+            int m = 0;
+            while (m < 4 && ((used >> m) & 1)) ++m;
+            if (m == 4) break;
+            used |= 1u << m;
+            t.st_swz[i] = int8_t(1 << m);
+        }
+    }
     t.nbk = int(op.b_pos_k.size());
     t.nbn = int(op.b_pos_n.size());
     for (int i = 0; i < t.nbk; ++i) t.bpk[i] = int8_t(op.b_pos_k[i]);
@@ -186,6 +206,7 @@ bool tc_grouped(const Analysis& an, const Op& op, const xebk::GemmDesc& d, xebk:
     if (!tc_tile(o2, t, xebk::kTc2RowBits, true)) return false;
     t.tma = 0;
     t.grp = 1;
+    std::memset(t.st_swz, 0, sizeof(t.st_swz));
     t.tpg = op.M >> xebk::kTc2RowBits;
     t.n_groups = d.n_groups;
     t.c_key = d.c_key;
@@ -1752,6 +1773,20 @@ extern "C" xeb_status xeb_plan_profile(xeb_plan_s* p, int enable) {
     p->op_ms.clear();
     p->op_n.clear();
     p->profiling = enable != 0;
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_op_layout(const xeb_plan_s* p, int op_index, int32_t* out, int cap, int32_t* n_out) {
+    if (!p || !n_out) return fail(XEB_EINVAL, "NULL plan or n_out");
+    if (op_index < 0 || size_t(op_index) >= p->prog.ops.size()) return fail(XEB_EINVAL, "op index out of range");
+    const Op& op = p->prog.ops[size_t(op_index)];
+    std::vector<int32_t> v = {op.kind, op.node, op.a_node, op.b_node};
+    const std::vector<int>* lists[6] = {&op.a_pos_m, &op.a_pos_k, &op.b_pos_k, &op.b_pos_n, &op.c_pos_m, &op.c_pos_n};
+    for (auto* l : lists) v.push_back(int32_t(l->size()));
+    for (auto* l : lists) v.insert(v.end(), l->begin(), l->end());
+    *n_out = int32_t(v.size());
+    if (out)
+        for (int i = 0; i < std::min(cap, int(v.size())); ++i) out[i] = v[size_t(i)];
     return XEB_OK;
 }
 

@@ -110,6 +110,11 @@ struct TcDesc {
     int Tst;
     uint32_t st_is_n;
     int8_t st_pos[16], st_idx[16];
+    // staging swizzle of the result tile (tensor-memory variant): element
+    // (row, n) of the tile is staged at float2 slot row * 64 + (n ^ x), where
+    // x is the XOR of st_swz[i] over the tile bits i (ascending C address
+    // order) set in (row, n); st_swz[i] < 16 and is 0 for column bits below 4
+    int8_t st_swz[16];
     float* wimg;          // scratch: split, swizzled image of the real-expanded B
     int32_t* err;         // error word (timeouts)
     // (tensor-memory variant, TMA mode) A is a row-major [M][K] matrix; a

@@ -53,7 +53,7 @@ constexpr int kRawBytes = kRows * 128;            // TMA mode: raw stage, 16 KB
 constexpr int kRingGather = 4;                    // operand stages, gather mode
 constexpr int kRingTma = 3;                       // operand stages, TMA mode
 constexpr int kRaw = 4;                           // raw stages, TMA mode (64 KB of loads in flight)
-constexpr int kCStride = 130;                     // floats per staged output row
+constexpr int kCStride = 128;                     // floats per staged output row (XOR-swizzled columns)
 constexpr uint32_t kTmemCols = 512;
 template <bool kTma>
 __host__ __device__ constexpr int op_stages() { return kTma ? kRingTma : kRingGather; }
@@ -176,6 +176,9 @@ __device__ __forceinline__ void tm_st32(uint32_t ta, const float* v) {
 struct Sm2 {
     uint64_t full[kRingGather], empty[kRingGather], rfull[kRaw], rempty[kRaw], tfull[2], tempty[2], wready, drain, epi;
     uint32_t tmem, pad;
+    // staging offset (floats) of tile row r = rlo[r % 32] ^ rhi[r / 32]: the
+    // row's base r * kCStride with its column swizzle folded in (linear in r)
+    int32_t rlo[32], rhi[kRows / 32];
 };
 
 }  // namespace
@@ -214,6 +217,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         bar_init(&S->wready, kEpiT);
         bar_init(&S->drain, 1);
         bar_init(&S->epi, kEpiT);
+    }
+    if (tid < 32 + kRows / 32) {
+        // x(r): XOR of the swizzle vectors of r's bits (tile row bit b is
+        // tile bit i with st_is_n clear and st_idx = b)
+        const int r = tid < 32 ? tid : (tid - 32) * 32;
+        int x = 0;
+        for (int i = 0; i < t.Tst; ++i)
+            if (!((t.st_is_n >> i) & 1) && ((r >> t.st_idx[i]) & 1)) x ^= int(t.st_swz[i]);
+        (tid < 32 ? S->rlo[tid] : S->rhi[tid - 32]) = (r * kCStride) ^ (2 * x);
+    }
+    if (tid == 0) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
@@ -468,15 +482,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         // keeps the increments of the block's low 3 bits in registers: eight
         // independent staging loads and stores per group, no table lookups.
         auto ginc = [&](int i) { return int64_t(1) << t.st_pos[i]; };
+        // staging slot (float2 units) of tile bit i: row r -> r * 64, column
+        // n -> n, each XOR its swizzle vector; slots combine by XOR
         auto sinc = [&](int i) {
-            return ((t.st_is_n >> i) & 1) ? (1 << t.st_idx[i]) : (1 << t.st_idx[i]) * (kCStride / 2);
+            return (((t.st_is_n >> i) & 1) ? (1 << t.st_idx[i]) : (1 << t.st_idx[i]) * (kCStride / 2)) ^
+                   int(t.st_swz[i]);
         };
+        // staging writes: the swizzle of each tile row bit, and the XOR of
+        // the swizzles of this thread's column bits (>= 4: one per warp)
+        int xn = 0;
+        for (int i = 0; i < t.Tst; ++i)
+            if (((t.st_is_n >> i) & 1) && (((np >> 1) >> t.st_idx[i]) & 1)) xn ^= int(t.st_swz[i]);
+        const int npx = np ^ (2 * xn);   // this thread's swizzled staging column
         int lo_slot = 0;
         int64_t lo_glob = 0;
         for (int i = 0; i < 5; ++i)  // Tst >= 11 (7 row bits + >= 4 column bits)
             if ((lane >> i) & 1) {
                 lo_glob += ginc(i);
-                lo_slot += sinc(i);
+                lo_slot ^= sinc(i);
             }
         constexpr int kWB = kEpiWarps == 8 ? 3 : 2;  // log2(epilogue warps)
         const int hb = t.Tst - 5;                    // bits of h
@@ -489,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < qb; ++i)
             if ((widx >> i) & 1) {
                 gq += ginc(5 + wb + i);
-                sq += sinc(5 + wb + i);
+                sq ^= sinc(5 + wb + i);
             }
         int64_t g8[8];
         int s8[8];
@@ -500,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int b = 0; b < lb; ++b)
                 if ((j >> b) & 1) {
                     g8[j] += ginc(5 + b);
-                    s8[j] += sinc(5 + b);
+                    s8[j] ^= sinc(5 + b);
                 }
         }
         const int nlo = 1 << lb, nmid = 1 << (wb - lb);
@@ -527,6 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t db = tmem + 256;
             constexpr int kMyRows = kRows / kShares;
             for (int r0 = half * kMyRows; r0 < (half + 1) * kMyRows; r0 += 32) {
+                const int cb = S->rhi[r0 >> 5] ^ npx;
                 float v[32], w[32];
                 tm_ld32(db + lanes + uint32_t(r0), v);
                 tm_ld32(db + lanes + kRows + uint32_t(r0), w);
@@ -536,7 +560,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     bar_arrive(&S->tempty[b]);
                 }
 #pragma unroll
-                for (int i = 0; i < 32; ++i) cst[(r0 + i) * kCStride + np] = v[i] + w[i];
+                for (int i = 0; i < 32; i += 4) {
+                    const int4 ro = *reinterpret_cast<const int4*>(&S->rlo[i]);
+                    cst[ro.x ^ cb] = v[i] + w[i];
+                    cst[ro.y ^ cb] = v[i + 1] + w[i + 1];
+                    cst[ro.z ^ cb] = v[i + 2] + w[i + 2];
+                    cst[ro.w ^ cb] = v[i + 3] + w[i + 3];
+                }
             }
             if (switch_w) {
                 write_wt(nxt);
@@ -564,12 +594,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int bb = 0; bb < wb - lb; ++bb)
                         if ((jm >> bb) & 1) {
                             gm += ginc(5 + lb + bb);
-                            sm2 += sinc(5 + lb + bb);
+                            sm2 ^= sinc(5 + lb + bb);
                         }
                     float2 v[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (j < nlo) v[j] = st2[sm2 + s8[j]];
+                        if (j < nlo) v[j] = st2[sm2 ^ s8[j]];
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
                         if (j < nlo) C[gm + g8[j]] = v[j];
@@ -581,11 +611,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int bb = 0; bb < wb - lb; ++bb)
                         if ((jm >> bb) & 1) {
                             gm += ginc(5 + lb + bb);
-                            sm2 += sinc(5 + lb + bb);
+                            sm2 ^= sinc(5 + lb + bb);
                         }
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (j < nlo && (sm2 + s8[j]) % (kCStride / 2) < nk) C[gm + g8[j]] = st2[sm2 + s8[j]];
+                        if (j < nlo && ((sm2 ^ s8[j]) & (kCStride / 2 - 1)) < nk) C[gm + g8[j]] = st2[sm2 ^ s8[j]];
                 }
             }
             if (!__all_sync(0xffffffffu, epi_sync())) break;
@@ -604,6 +634,7 @@ template <bool kTma>
 constexpr size_t tc2_smem() {
     return 1024 + ring_bytes<kTma>() + size_t(kRows) * kCStride * 4 + sizeof(Sm2);
 }
+static_assert(offsetof(Sm2, rlo) % 16 == 0, "row table read as int4");
 static_assert(sizeof(Sm2) % 8 == 0 && tc2_smem<true>() <= 232448 && tc2_smem<false>() <= 232448,
               "tensor-memory contraction exceeds the shared memory of one CTA");
 
