@@ -991,6 +991,52 @@ __global__ void k_memo_prep(const __grid_constant__ GemmDesc g, const T* __restr
     }
 }
 
+// Rows x keys of one memo-level tile with K = 16 (complex64): thread tid
+// takes row tid % R (R < 256: 256 / R threads share a row and take every
+// (256 / R)-th key) and keeps the row's 16 values in registers; the keys'
+// B vectors (16 values each, 16-byte aligned) are read two values at a time.
+// C points at (first key of the batch, first row of the tile); key j's row r
+// is C[j * c_key + r].
+__device__ __forceinline__ void memo_rows_k16(const float2* __restrict__ cur, int ldA, const float2* __restrict__ Bv,
+                                              float2* __restrict__ C, int64_t c_key, int R, int rows, int nb) {
+    const int tid = threadIdx.x;
+    const int S = R >= 256 ? 1 : 256 / R;
+    const int rs = R >= 256 ? 256 : R;
+    const int j0 = R >= 256 ? 0 : tid / R;
+    for (int r = R >= 256 ? tid : tid % R; r < rows; r += rs) {
+        float2 a[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = cur[k * ldA + r];
+        int j = j0;
+        for (; j + S < nb; j += 2 * S) {
+            const float4* b0 = reinterpret_cast<const float4*>(Bv + j * 16);
+            const float4* b1 = reinterpret_cast<const float4*>(Bv + (j + S) * 16);
+            float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const float4 q0 = b0[kk], q1 = b1[kk];
+                c0 = cfma(c0, a[2 * kk], make_float2(q0.x, q0.y));
+                c0 = cfma(c0, a[2 * kk + 1], make_float2(q0.z, q0.w));
+                c1 = cfma(c1, a[2 * kk], make_float2(q1.x, q1.y));
+                c1 = cfma(c1, a[2 * kk + 1], make_float2(q1.z, q1.w));
+            }
+            C[j * c_key + r] = c0;
+            C[(j + S) * c_key + r] = c1;
+        }
+        if (j < nb) {
+            const float4* b0 = reinterpret_cast<const float4*>(Bv + j * 16);
+            float2 c0 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const float4 q0 = b0[kk];
+                c0 = cfma(c0, a[2 * kk], make_float2(q0.x, q0.y));
+                c0 = cfma(c0, a[2 * kk + 1], make_float2(q0.z, q0.w));
+            }
+            C[j * c_key + r] = c0;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, 2) k_gemm_memo(const __grid_constant__ GemmDesc g,
                                                       const __grid_constant__ StreamDesc s, T* __restrict__ arena,
@@ -1102,7 +1148,14 @@ __global__ void __launch_bounds__(256, 2) k_gemm_memo(const __grid_constant__ Ge
                 __syncthreads();
                 Bv = Bs;
             }
-            if (K <= 16) {
+            if (sizeof(T) == 8 && K == 16) {
+                // the memo-trie levels of grid plans: 16 summed values (four
+                // output bits), complex64.  Compile-time K, B read as float4,
+                // two keys per pass over the row's values in registers
+                memo_rows_k16(reinterpret_cast<const float2*>(cur), ldA, reinterpret_cast<const float2*>(Bv),
+                              reinterpret_cast<float2*>(arena) + g.c_off + ub0 * g.c_key + mt * R, g.c_key,
+                              R, rows, nb);
+            } else if (K <= 16) {
                 const int S = R >= 256 ? 1 : 256 / R;   // threads per row
                 const int rs = R >= 256 ? 256 : R;
                 for (int r = R >= 256 ? tid : tid % R; r < rows; r += rs) {
