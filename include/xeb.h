@@ -182,7 +182,10 @@ xeb_status xeb_plan_tree(struct xeb_plan_s* plan, int32_t* children, int32_t* sl
 xeb_status xeb_plan_node(struct xeb_plan_s* plan, int node, int64_t* kv, int32_t* a,
                          int32_t* b, int32_t* n_legs, int32_t* n_shared);
 
-/* Device memory the plan needs (bytes) for xeb_plan_bind. */
+/* Device memory the plan needs (bytes) for xeb_plan_bind.  Tensor sizes
+ * saturate at 2^48 elements, so a plan with a wider intermediate reports a
+ * huge but finite size (below 2^62) and xeb_plan_bind refuses it with
+ * XEB_ENOMEM before touching the device. */
 size_t xeb_plan_device_bytes(struct xeb_plan_s* plan);
 
 /* Attach device memory and upload the plan's constant tables on `stream`.

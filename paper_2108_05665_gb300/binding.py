@@ -452,6 +452,11 @@ class Plan:
     def bind(self, device="cuda"):
         import torch
         nbytes = xeb_plan_device_bytes(self.handle)
+        dev = torch.device(device)
+        total = torch.cuda.get_device_properties(dev.index if dev.index is not None else torch.cuda.current_device()).total_memory
+        if nbytes + 256 > total:
+            raise XebError(2, "plan needs %.3g GB of device memory, the device has %.3g GB"
+                           % (nbytes / 1e9, total / 1e9))
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
         ptr = self.workspace.data_ptr()
         ptr = (ptr + 255) // 256 * 256

@@ -606,9 +606,9 @@ void plan_features(const Candidate& c, size_t n_sliced, const xeb_plan_opts& o, 
     for (const Op& op : c.prog.ops) {
         if (op.kind == OP_PERM) continue;
         const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
-        const double by = double(elem) * (double(c.an.nodes[op.a_node].kv) * double(op.M * op.K) +
-                                          double(c.an.nodes[op.b_node].kv) * double(op.K * op.N) +
-                                          double(op.kv) * double(op.M * op.N));
+        const double by = double(elem) * (double(c.an.nodes[op.a_node].kv) * double(op.M) * double(op.K) +
+                                          double(c.an.nodes[op.b_node].kv) * double(op.K) * double(op.N) +
+                                          double(op.kv) * double(op.M) * double(op.N));
         xebk::StreamDesc sd;
         int cl;
         if (tf32 && tc_eligible(op)) cl = 0;
@@ -1377,8 +1377,8 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 const GemmLaunch& g = p->gemms[i];
                 const double ka = double(an.nodes[op.a_node].kv), kb = double(an.nodes[op.b_node].kv);
                 const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
-                const double by = es * (ka * double(op.M * op.K) + kb * double(op.K * op.N) +
-                                        double(op.kv) * double(op.M * op.N));
+                const double by = es * (ka * double(op.M) * double(op.K) + kb * double(op.K) * double(op.N) +
+                                        double(op.kv) * double(op.M) * double(op.N));
                 static const int cls_of[7] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
                                               XEB_KC_GEMM_TAIL,    XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO,
                                               XEB_KC_GEMM_KDEEP};
@@ -1437,6 +1437,9 @@ extern "C" size_t xeb_plan_device_bytes(xeb_plan_s* p) {
 extern "C" xeb_status xeb_plan_bind(xeb_plan_s* p, void* workspace, size_t bytes, uintptr_t stream) {
     if (!p) return fail(XEB_EINVAL, "NULL plan");
     if (p->bound) return fail(XEB_EINVAL, "plan already bound");
+    for (const Buffer& b : p->prog.bufs)
+        if (b.elems >= xebp::kSatElems)
+            return fail(XEB_ENOMEM, "plan has a tensor of 2^48 or more elements: it fits no device (slice more legs)");
     layout_device(p);
     {
         int dev = 0, sms = 0;

@@ -337,7 +337,7 @@ void build_program(const Analysis& an, Program& prog, bool gather, bool consumer
         prog.bufs.push_back(b);
         return int(prog.bufs.size()) - 1;
     };
-    auto elems_of = [&](int v) { return an.nodes[v].kv * (int64_t(1) << an.nodes[v].legs.size()); };
+    auto elems_of = [&](int v) { return mul_sat(an.nodes[v].kv, pow2_sat(an.nodes[v].legs.size())); };
     // leaves are materialised in their canonical leg order
     for (int j = 0; j < L; ++j) {
         prog.layout[j] = an.nodes[j].legs;
@@ -433,9 +433,9 @@ void build_program(const Analysis& an, Program& prog, bool gather, bool consumer
             const int leg = lb[op.b_rank - 1 - b];
             if (!inS[leg]) { fb.push_back(leg); op.b_pos_n.push_back(b); }
         }
-        op.M = int64_t(1) << fa.size();
-        op.N = int64_t(1) << fb.size();
-        op.K = int64_t(1) << sg.size();
+        op.M = pow2_sat(fa.size());
+        op.N = pow2_sat(fb.size());
+        op.K = pow2_sat(sg.size());
         op.kv = nd.kv;
         const int idx = int(prog.ops.size()) + 1;
         op.c_buf = new_buf(elems_of(v), idx);
@@ -481,7 +481,7 @@ void plan_memory(Program& prog) {
     int64_t peak = 0;
     for (int t = 0; t < T; ++t) {
         for (int bi : born[t]) {
-            const int64_t len = (prog.bufs[bi].elems + align - 1) / align * align;
+            const int64_t len = (std::min(prog.bufs[bi].elems, kSatElems) + align - 1) / align * align;
             int64_t pos = 0;
             for (auto& kv : live) {
                 if (kv.first - pos >= len) break;
@@ -493,7 +493,7 @@ void plan_memory(Program& prog) {
         }
         for (int bi : dies[t]) live.erase(prog.bufs[bi].off);
     }
-    prog.arena_elems = peak;
+    prog.arena_elems = std::min(peak, kSatElems << 8);   // bytes stay below 2^61
 }
 
 Costs tree_costs(const Analysis& an, const Program& prog, uint64_t k) {

@@ -2,6 +2,7 @@
 // memoized evaluation counts, slicing, operand layouts and the device program.
 #pragma once
 
+#include <algorithm>
 #include <array>
 #include <complex>
 #include <cstdint>
@@ -36,6 +37,17 @@ struct Network {
 bool build_network(const xeb_circuit* c, Network& net, std::string& err);
 
 using Tree = std::vector<std::array<int, 2>>;  // post-order (left, right) pairs
+
+// Tensor and index sizes saturate at 2^48 elements (2 PiB of complex64: no
+// device holds one), so candidate trees with very wide intermediates cannot
+// overflow the planner's integer arithmetic; a plan that reaches the bound
+// is refused at bind (XEB_ENOMEM).
+constexpr int64_t kSatElems = int64_t(1) << 48;
+inline int64_t pow2_sat(size_t b) { return b >= 48 ? kSatElems : int64_t(1) << b; }
+inline int64_t mul_sat(int64_t a, int64_t b) {
+    if (a <= 0 || b <= 0) return 0;
+    return a > kSatElems / b ? kSatElems : std::min(a * b, kSatElems);
+}
 
 // Per tree node (uniform ids: leaf j -> j, internal i -> L + i).
 struct Node {

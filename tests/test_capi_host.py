@@ -182,3 +182,30 @@ def test_slice_subset_is_seeded_and_distinct():
             B.xeb_set_slice_subset(p, 0.0, 1)
     finally:
         B.xeb_plan_destroy(p)
+
+
+def test_wide_plan_saturates_and_is_refused_at_bind(lib):
+    """A tree that first joins every output leaf of a 40-qubit circuit (300
+    distinct keys) and then absorbs the other leaves from the last gate
+    backwards carries ~300 keys x 2^40 elements: no device holds it.  Its
+    sizes saturate at 2^48 elements per tensor (a finite byte count below
+    2^62, no integer overflow) and binding refuses it with XEB_ENOMEM before
+    any device call."""
+    w = inputs.WORKLOADS["grid5x8_m12_k100000"]
+    circ = w.circuit()
+    bits = inputs.uniform_bitstrings(circ.n_qubits, 300, 11)
+    outq, _ = B.xeb_network_leaves(circ)
+    order = [j for j in range(len(outq)) if outq[j]] + [j for j in range(len(outq)) if not outq[j]][::-1]
+    tree = [(-1 - order[0], -1 - order[1])] + [(i - 1, -1 - order[i + 1]) for i in range(1, len(order) - 1)]
+    o = B.xeb_default_opts()
+    o.precision = B.XEB_PREC_FP32
+    plan = B.xeb_plan_create(circ, bits, tree=tree, slices=[], opts=o)
+    try:
+        nbytes = B.xeb_plan_device_bytes(plan)
+        assert 8 * 2 ** 48 <= nbytes < 2 ** 62
+        assert B.xeb_plan_stats(plan)["arena_bytes"] >= 8 * 2 ** 48
+        with pytest.raises(B.XebError) as e:
+            B.xeb_plan_bind(plan, 0, 0, 0)
+        assert e.value.status == 2
+    finally:
+        B.xeb_plan_destroy(plan)
