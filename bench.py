@@ -220,13 +220,16 @@ def main():
     ap.add_argument("--tc-loads", default="tma", choices=["tma", "gather"],
                     help="tensor-core A operand: TMA boxes where A is row-major (default) or plain-load gathers")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid5x5_m12_k2000", "grid3x9_m12_k2000",
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "grid3x4_m8_k1000", "grid5x5_m12_k2000", "grid3x9_m12_k2000",
                                                           "grid5x8_m12_k100000", "grid6x9m1_m12_k300000",
                                                           "grid6x9m1_m14_k1000000"],
                     help="benchmark workload (default), the small profiling cases, or the sliced 40/53-qubit ones")
     ap.add_argument("--slice-frac", type=float, default=None,
                     help="run a seeded subset of the slices (partial sums) and extrapolate amplitudes/s by 1/frac; "
-                         "default: all slices, except 1/16 (40 qubits) and 1%% (53 qubits)")
+                         "default: all slices, except 1/16 (40 qubits)")
+    ap.add_argument("--slices", type=int, default=None,
+                    help="run this many seeded slices (partial sums) and extrapolate; default 4 for the 53-qubit "
+                         "workloads, whose plans have millions of slices of several TFLOP each")
     ap.add_argument("--mem-gb", type=float, default=None,
                     help="planner memory budget in GB (default 64 GiB; 200 for the 53-qubit workloads)")
     args = ap.parse_args()
@@ -254,8 +257,10 @@ def main():
         o.mem_budget = int(args.mem_gb * 2 ** 30)
     elif w.n_qubits > 40:
         o.mem_budget = 200 << 30
-    if args.slice_frac is None and big:
-        args.slice_frac = 1.0 / 16 if w.n_qubits <= 40 else 0.01
+    if args.slices is None and args.slice_frac is None and w.n_qubits > 40:
+        args.slices = 4
+    if args.slice_frac is None and big and args.slices is None:
+        args.slice_frac = 1.0 / 16
     chosen = None
     if args.planner == "learned":
         from paper_2108_05665_gb300 import costmodel
@@ -284,6 +289,8 @@ def main():
 
     frac = 1.0
     n_run = st["n_slices"]
+    if args.slices is not None and args.slices < n_run:
+        args.slice_frac = args.slices / float(n_run)
     if args.slice_frac is not None and args.slice_frac < 1.0:
         n_run = B.xeb_set_slice_subset(plan.handle, args.slice_frac, 12345)
         frac = n_run / st["n_slices"]
