@@ -169,6 +169,24 @@ xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t* bitstring
                            const xeb_tree* tree, const xeb_slices* slices,
                            const xeb_plan_opts* opts, struct xeb_plan_s** out);
 
+/* Multi-batch plan (Sec. "Multi-batch simulator"): the output legs of the
+ * qubits set in open_mask (bit q = qubit q) are not contracted, so every
+ * input bitstring stands for the batch of 2^w bitstrings (w = popcount of
+ * open_mask, 1 <= w <= 16, w < n) that share its other bits; its open bits are
+ * ignored.  xeb_amplitudes then writes k x 2^w complex128 values,
+ * out[i * 2^w + x] = <s_i with the open qubits set to x | C | 0^n>, where bit j
+ * of x is the j-th open qubit in ascending order; xeb_fidelity's F, mean of
+ * 2^n p and mean of (2^n p)^2 run over those k 2^w values (Eq. 1 over the
+ * batches' bitstrings).  The network is the one of xeb_network_leaves with
+ * each open qubit's output bit turned into a leg of its own (ids n_legs ..
+ * n_legs + w - 1, ascending qubit order; bond legs keep their ids), so trees
+ * and slices of the plain network apply; an open leg cannot be sliced
+ * (XEB_EINVAL).  Other arguments, ownership and errors as xeb_plan_create;
+ * XEB_EINVAL for an open qubit >= n, XEB_EUNSUPPORTED for w > 16 or w = n. */
+xeb_status xeb_plan_create_batched(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                                   uint64_t open_mask, const xeb_tree* tree, const xeb_slices* slices,
+                                   const xeb_plan_opts* opts, struct xeb_plan_s** out);
+
 void xeb_plan_destroy(struct xeb_plan_s* plan);
 
 /* Statistics of a plan (host only). */
@@ -204,7 +222,8 @@ xeb_status xeb_set_bitstrings(struct xeb_plan_s* plan, const uint64_t* bitstring
 
 /* One step: build the key tables of the current bitstrings (a1), contract
  * every slice (a2..a6) and write the k amplitudes, in input order, as
- * complex128 to device memory out_dev [2*k doubles] (NULL: the plan's own
+ * complex128 to device memory out_dev [2*k doubles; 2*k*2^w for a
+ * multi-batch plan, see xeb_plan_create_batched] (NULL: the plan's own
  * buffer), plus the XEB sums (a7).  The first call per output pointer
  * captures the step as a CUDA graph on a private stream; later calls replay
  * it on `stream` (not while profiling, or with opts.reserved[2] = 1). */
@@ -235,7 +254,8 @@ xeb_status xeb_fidelity(struct xeb_plan_s* plan, double* F, double* mean_2np,
 
 /* End to end from host memory: copy bitstrings_host [k] (pinned for async
  * speed) to the device, build key tables, contract, copy amplitudes
- * [2*k doubles] and F to host.  Synchronises. */
+ * [2*k doubles; 2*k*2^w for a multi-batch plan] and F to host.
+ * Synchronises. */
 xeb_status xeb_run(struct xeb_plan_s* plan, const uint64_t* bitstrings_host, size_t k,
                    double* amps_host, double* F_host, uintptr_t stream);
 

@@ -117,6 +117,9 @@ _PROTOS = {
     "xeb_set_slice_subset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64,
                                             ctypes.POINTER(ctypes.c_int64)]),
     "xeb_plan_slice_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "xeb_plan_create_batched": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _u64p, ctypes.c_size_t, ctypes.c_uint64,
+                                               ctypes.POINTER(xeb_tree), ctypes.POINTER(xeb_slices),
+                                               ctypes.POINTER(xeb_plan_opts), ctypes.POINTER(ctypes.c_void_p)]),
     "xeb_plan_op_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, ctypes.c_int, _i32p]),
     "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
                                             ctypes.POINTER(ctypes.c_int32)]),
@@ -192,7 +195,8 @@ def xeb_network_leaves(circuit):
 
 
 def xeb_plan_create(circuit, bitstrings, tree: Optional[Sequence] = None, slices: Optional[Sequence[int]] = None,
-                    opts: Optional[xeb_plan_opts] = None) -> ctypes.c_void_p:
+                    opts: Optional[xeb_plan_opts] = None, open_qubits: Optional[Sequence[int]] = None) -> ctypes.c_void_p:
+    """xeb_plan_create, or xeb_plan_create_batched when open_qubits is given."""
     ca = CircuitArrays(circuit)
     bs = np.ascontiguousarray(bitstrings, dtype=np.uint64)
     tp = None
@@ -206,8 +210,16 @@ def xeb_plan_create(circuit, bitstrings, tree: Optional[Sequence] = None, slices
         s = xeb_slices(len(sl), _ptr(sl, ctypes.c_int32))
         sp = ctypes.byref(s)
     out = ctypes.c_void_p()
-    _check(load().xeb_plan_create(ctypes.byref(ca.c), _ptr(bs, ctypes.c_uint64), len(bs), tp, sp,
-                                  ctypes.byref(opts) if opts is not None else None, ctypes.byref(out)))
+    op = ctypes.byref(opts) if opts is not None else None
+    if open_qubits is not None:
+        mask = 0
+        for q in open_qubits:
+            mask |= 1 << int(q)
+        _check(load().xeb_plan_create_batched(ctypes.byref(ca.c), _ptr(bs, ctypes.c_uint64), len(bs), mask, tp, sp,
+                                              op, ctypes.byref(out)))
+    else:
+        _check(load().xeb_plan_create(ctypes.byref(ca.c), _ptr(bs, ctypes.c_uint64), len(bs), tp, sp, op,
+                                      ctypes.byref(out)))
     return out
 
 
@@ -437,10 +449,11 @@ def xeb_plan_profile_read(plan) -> dict:
 class Plan:
     """Owner of one xeb_plan handle plus the torch buffers it is bound to."""
 
-    def __init__(self, circuit, bitstrings, tree=None, slices=None, opts=None):
-        self.handle = xeb_plan_create(circuit, bitstrings, tree, slices, opts)
+    def __init__(self, circuit, bitstrings, tree=None, slices=None, opts=None, open_qubits=None):
+        self.handle = xeb_plan_create(circuit, bitstrings, tree, slices, opts, open_qubits)
         self.k = len(bitstrings)
         self.n = circuit.n_qubits
+        self.w = len(set(open_qubits)) if open_qubits is not None else 0   # 2^w amplitudes per bitstring
         self.workspace = None
 
     def stats(self):

@@ -227,7 +227,7 @@ struct Annealer {
             int bl = -1;
             double bm = 0, bf = 0;
             for (int l = 0; l < net.n_legs; ++l) {
-                if (!cand[l]) continue;
+                if (!cand[l] || net.is_open_leg(l)) continue;
                 sl[l] = 1;
                 ++n_sliced;
                 recompute();

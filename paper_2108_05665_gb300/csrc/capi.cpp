@@ -288,6 +288,8 @@ bool stream_tile(const Op& op, size_t elem, xebk::StreamDesc& s) {
 
 struct xeb_plan_s {
     Network net;
+    int w = 0;               // open qubits (multi-batch): 2^w amplitudes per bitstring
+    xebk::RootMap rootmap{};  // where open-qubit bit j sits in the root's per-key block
     Tree tree;
     std::vector<int> sliced;
     Analysis an;
@@ -656,9 +658,9 @@ void plan_features(const Candidate& c, size_t n_sliced, const xeb_plan_opts& o, 
 
 }  // namespace
 
-extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
-                                      const xeb_tree* tree, const xeb_slices* slices,
-                                      const xeb_plan_opts* opts, xeb_plan_s** out) {
+namespace {
+xeb_status create_plan(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k, uint64_t open_mask,
+                       const xeb_tree* tree, const xeb_slices* slices, const xeb_plan_opts* opts, xeb_plan_s** out) {
     if (!out) return fail(XEB_EINVAL, "out is NULL");
     *out = nullptr;
     if (k == 0 || !bitstrings) return fail(XEB_EINVAL, "need k >= 1 bitstrings");
@@ -672,7 +674,10 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
         return fail(XEB_EINVAL, "unknown precision");
     p->elem = o.precision == XEB_PREC_FP64 ? 16 : 8;
     std::string err;
-    if (!build_network(circuit, p->net, err)) return fail(XEB_EINVAL, err);
+    if (!build_network(circuit, p->net, err, open_mask)) return fail(XEB_EINVAL, err);
+    p->w = p->net.n_open;
+    if (p->w > 16) return fail(XEB_EUNSUPPORTED, "more than 16 open qubits");
+    if (p->w == p->net.n) return fail(XEB_EUNSUPPORTED, "every qubit open: nothing to memoize (use a state vector)");
     const int n = p->net.n;
     for (size_t i = 0; i < k; ++i)
         if (n < 64 && (bitstrings[i] >> n) != 0) return fail(XEB_EINVAL, "bitstring has bits above n");
@@ -765,8 +770,30 @@ extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t
     p->prog = std::move(best.prog);
     p->costs = best.costs;
     p->objective = best.f;
+    {   // the root's block: its legs are exactly the open legs
+        const std::vector<int>& lay = p->prog.layout[p->an.nodes.size() - 1];
+        if (int(lay.size()) != p->w) return fail(XEB_EINVAL, "internal: root legs differ from the open legs");
+        p->rootmap.w = p->w;
+        for (int j = 0; j < p->w; ++j) {
+            const int at = int(std::find(lay.begin(), lay.end(), p->net.open_legs[size_t(j)]) - lay.begin());
+            p->rootmap.pos[j] = int8_t(int(lay.size()) - 1 - at);
+        }
+    }
     *out = p.release();
     return XEB_OK;
+}
+}  // namespace
+
+extern "C" xeb_status xeb_plan_create(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                                      const xeb_tree* tree, const xeb_slices* slices,
+                                      const xeb_plan_opts* opts, xeb_plan_s** out) {
+    return create_plan(circuit, bitstrings, k, 0, tree, slices, opts, out);
+}
+
+extern "C" xeb_status xeb_plan_create_batched(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                                              uint64_t open_mask, const xeb_tree* tree, const xeb_slices* slices,
+                                              const xeb_plan_opts* opts, xeb_plan_s** out) {
+    return create_plan(circuit, bitstrings, k, open_mask, tree, slices, opts, out);
 }
 
 extern "C" xeb_status xeb_plan_candidates(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
@@ -959,8 +986,8 @@ void layout_device(xeb_plan_s* p) {
         d.r_key_off = tr >= 0 ? p->trie[tr].key_off : -1;
         p->trie_internal.push_back(ti);
     }
-    p->t_acc = take(an.nodes[N - 1].kv * 16);
-    p->t_amps = take(int64_t(p->k) * 16);
+    p->t_acc = take((an.nodes[N - 1].kv << p->w) * 16);
+    p->t_amps = take((int64_t(p->k) << p->w) * 16);
     p->t_partials = take(int64_t(p->n_xeb_blocks) * 16);
     p->t_result = take(64);
     p->t_err = take(16);
@@ -1357,7 +1384,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
     const T* leafdata = reinterpret_cast<const T*>(p->ws + p->off_leafdata);
     double2* acc = reinterpret_cast<double2*>(tables + p->t_acc);
     const int64_t kv_root = an.nodes.back().kv;
-    XEB_CUDA(cudaMemsetAsync(acc, 0, size_t(kv_root) * 16, st));
+    XEB_CUDA(cudaMemsetAsync(acc, 0, size_t(kv_root << p->w) * 16, st));
     const int64_t n_run = p->slice_ids.empty() ? int64_t(1) << p->sliced.size() : int64_t(p->slice_ids.size());
     const auto* ldesc = reinterpret_cast<const xebk::LeafDesc*>(tables + p->t_leaf_desc);
     const double es = double(sizeof(T));
@@ -1387,14 +1414,14 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
             }
         }
         {
-            ProfScope ps(p, st, XEB_KC_ACCUM, 0.0, double(kv_root) * (16.0 + 2 * es));
-            XEB_CUDA(xebk::launch_root_accum<T>(arena + pr.bufs[pr.node_buf.back()].off, acc, kv_root, st));
+            ProfScope ps(p, st, XEB_KC_ACCUM, 0.0, double(kv_root << p->w) * (16.0 + 2 * es));
+            XEB_CUDA(xebk::launch_root_accum<T>(arena + pr.bufs[pr.node_buf.back()].off, acc, kv_root << p->w, st));
         }
     }
     const int troot = p->trie_of_node[int(an.nodes.size()) - 1];
     const int32_t* key_root = reinterpret_cast<const int32_t*>(tables + p->trie[troot].key_off);
-    ProfScope ps(p, st, XEB_KC_XEB, 0.0, double(p->k) * 36.0);
-    XEB_CUDA(xebk::launch_gather_xeb(acc, key_root, int64_t(p->k), amps_out,
+    ProfScope ps(p, st, XEB_KC_XEB, 0.0, double(p->k) * 4.0 + double(p->k << p->w) * 32.0);
+    XEB_CUDA(xebk::launch_gather_xeb(acc, key_root, int64_t(p->k), p->rootmap, amps_out,
                                      reinterpret_cast<double*>(tables + p->t_partials), p->n_xeb_blocks,
                                      reinterpret_cast<double*>(tables + p->t_result), p->net.n, st));
     return XEB_OK;
@@ -1671,7 +1698,7 @@ extern "C" xeb_status xeb_run(xeb_plan_s* p, const uint64_t* bits_host, size_t k
     double* amps_dev = reinterpret_cast<double*>(tables + p->t_amps);
     s = xeb_amplitudes(p, amps_dev, stream);
     if (s != XEB_OK) return s;
-    if (amps_host) XEB_CUDA(cudaMemcpyAsync(amps_host, amps_dev, k * 16, cudaMemcpyDeviceToHost, st));
+    if (amps_host) XEB_CUDA(cudaMemcpyAsync(amps_host, amps_dev, (k << p->w) * 16, cudaMemcpyDeviceToHost, st));
     return xeb_fidelity(p, F, nullptr, nullptr, stream);
 }
 

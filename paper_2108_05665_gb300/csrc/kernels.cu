@@ -1256,13 +1256,21 @@ cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStrea
     return cudaGetLastError();
 }
 
+// amps[i * 2^w + x] = the root value of bitstring i's key at open-qubit
+// value x; block partial sums of p and p^2 over all k 2^w values.
 __global__ void __launch_bounds__(256) k_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k,
-                                                    double2* amps, double* partials) {
+                                                    const RootMap rm, double2* amps, double* partials) {
     __shared__ double s1[256], s2[256];
     double a1 = 0.0, a2 = 0.0;
-    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < k; i += int64_t(gridDim.x) * blockDim.x) {
-        const double2 a = acc[key_root[i]];
-        amps[i] = a;
+    const int64_t total = k << rm.w;
+    const int64_t xmask = (int64_t(1) << rm.w) - 1;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t x = e & xmask;
+        int64_t off = 0;
+        for (int j = 0; j < rm.w; ++j)
+            if ((x >> j) & 1) off |= int64_t(1) << rm.pos[j];
+        const double2 a = acc[(int64_t(key_root[e >> rm.w]) << rm.w) + off];
+        amps[e] = a;
         const double p = a.x * a.x + a.y * a.y;
         a1 += p;
         a2 += p * p;
@@ -1310,12 +1318,13 @@ __global__ void __launch_bounds__(256) k_xeb_final(const double* partials, int n
     }
 }
 
-cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k, double2* amps,
-                              double* partials, int n_blocks, double* result, int n_qubits, cudaStream_t st) {
-    k_gather_xeb<<<n_blocks, 256, 0, st>>>(acc, key_root, k, amps, partials);
+cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k, const RootMap& rm,
+                              double2* amps, double* partials, int n_blocks, double* result, int n_qubits,
+                              cudaStream_t st) {
+    k_gather_xeb<<<n_blocks, 256, 0, st>>>(acc, key_root, k, rm, amps, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_xeb_final<<<1, 256, 0, st>>>(partials, n_blocks, k, n_qubits, result);
+    k_xeb_final<<<1, 256, 0, st>>>(partials, n_blocks, k << rm.w, n_qubits, result);
     return cudaGetLastError();
 }
 

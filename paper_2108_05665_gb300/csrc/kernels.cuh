@@ -176,7 +176,14 @@ cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream
 // tile bits = 6 row bits + 4 k bits).
 // tmap: 2-D tensor map of A (used when t.tma != 0)
 cudaError_t launch_tc_gemm2(const TcDesc& t, const CUtensorMap& tmap, float2* arena, int n_sms, cudaStream_t st);
-cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k,
+// Multi-batch plans: the root tensor of each key holds 2^w values, one per
+// value x of the open qubits; bit j of x (open qubits in ascending order)
+// sits at address bit pos[j] of the root's block.  w = 0: one value per key.
+struct RootMap {
+    int w;
+    int8_t pos[16];
+};
+cudaError_t launch_gather_xeb(const double2* acc, const int32_t* key_root, int64_t k, const RootMap& rm,
                               double2* amps, double* partials, int n_blocks, double* result,
                               int n_qubits, cudaStream_t st);
 

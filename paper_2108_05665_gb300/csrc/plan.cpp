@@ -82,10 +82,11 @@ int find_label(const RawLeaf& r, int kind, int id) {
 }
 }  // namespace
 
-bool build_network(const xeb_circuit* c, Network& net, std::string& err) {
+bool build_network(const xeb_circuit* c, Network& net, std::string& err, uint64_t open_mask) {
     if (!c) { err = "circuit is NULL"; return false; }
     const int n = c->n_qubits;
     if (n < 1 || n > 64) { err = "n_qubits must be in [1, 64]"; return false; }
+    if (n < 64 && (open_mask >> n) != 0) { err = "open qubit above n"; return false; }
     if (c->n_gates < 0 || (c->n_gates > 0 && (!c->kinds || !c->q0 || !c->mats))) {
         err = "circuit arrays missing";
         return false;
@@ -138,20 +139,29 @@ bool build_network(const xeb_circuit* c, Network& net, std::string& err) {
         raw.push_back(std::move(lf));
         last[a] = last[b] = int(raw.size()) - 1;
     }
+    // output side of every qubit: projected on the bitstring's bit, or (open
+    // qubits) a leg of its own, numbered after all bond legs
+    const int n_bond = next_leg;
+    net.open_legs.clear();
     for (int q = 0; q < n; ++q) {
+        const bool open = (open_mask >> q) & 1;
+        const std::pair<int, int> lab = open ? std::pair<int, int>{LAB_LEG, next_leg} : std::pair<int, int>{LAB_BIT, q};
+        if (open) net.open_legs.push_back(next_leg++);
         if (last[q] < 0) {
             RawLeaf lf;
             lf.t = {init[q][0], init[q][1]};
-            lf.lab = {{LAB_BIT, q}};
+            lf.lab = {lab};
             lf.qubits = {q};
             raw.push_back(std::move(lf));
         } else {
             RawLeaf& p = raw[last[q]];
-            p.lab[find_label(p, LAB_OUT, q)] = {LAB_BIT, q};
+            p.lab[find_label(p, LAB_OUT, q)] = lab;
         }
     }
     net.n = n;
     net.n_legs = next_leg;
+    net.open_mask = open_mask;
+    net.n_open = next_leg - n_bond;
     net.leaves.clear();
     for (RawLeaf& r : raw) {
         Leaf lf;
@@ -199,6 +209,7 @@ bool analyze(const Network& net, const Tree& tree, const std::vector<int>& slice
     for (int l : sliced) {
         if (l < 0 || l >= net.n_legs) { err = "sliced leg out of range"; return false; }
         if (is_sliced[l]) { err = "sliced leg listed twice"; return false; }
+        if (net.is_open_leg(l)) { err = "an open output leg cannot be sliced"; return false; }
         is_sliced[l] = 1;
     }
     an.L = L;
@@ -248,7 +259,7 @@ bool analyze(const Network& net, const Tree& tree, const std::vector<int>& slice
         nd.b = an.nodes[nd.r].b;
     };
     walk(L + int(tree.size()) - 1);
-    if (int(an.pi.size()) != net.n) { err = "internal: pi is not a permutation"; return false; }
+    if (int(an.pi.size()) != net.n - net.n_open) { err = "internal: pi is not a permutation"; return false; }
     return true;
 }
 

@@ -32,9 +32,18 @@ struct Network {
     int n = 0;
     int n_legs = 0;
     std::vector<Leaf> leaves;
+    // Multi-batch networks (Sec. "Multi-batch simulator"): the output legs of
+    // the qubits in open_mask are left uncontracted.  They are the legs
+    // n_legs - n_open .. n_legs - 1, one per open qubit in ascending qubit
+    // order (open_legs), each held by a single leaf, so they survive to the
+    // root; bond legs keep the ids they have without open qubits.
+    uint64_t open_mask = 0;
+    int n_open = 0;
+    std::vector<int> open_legs;
+    bool is_open_leg(int l) const { return l >= n_legs - n_open; }
 };
 
-bool build_network(const xeb_circuit* c, Network& net, std::string& err);
+bool build_network(const xeb_circuit* c, Network& net, std::string& err, uint64_t open_mask = 0);
 
 using Tree = std::vector<std::array<int, 2>>;  // post-order (left, right) pairs
 

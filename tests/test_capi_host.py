@@ -209,3 +209,40 @@ def test_wide_plan_saturates_and_is_refused_at_bind(lib):
         assert e.value.status == 2
     finally:
         B.xeb_plan_destroy(plan)
+
+
+def test_batched_plan_root_holds_the_open_legs(lib):
+    """Multi-batch plans (Sec. "Multi-batch simulator"): the w open output
+    legs are never summed, so the root tensor carries exactly them, its pi
+    range covers the n - w projected qubits, and its evaluation count is the
+    number of distinct values of the projected bits (the open bits of the
+    input bitstrings are ignored)."""
+    circ = inputs.random_grid_circuit(3, 4, 8, 808)
+    bits = inputs.uniform_bitstrings(12, 400, 909)
+    open_q = [1, 6, 10]
+    mask = sum(1 << q for q in open_q)
+    o = B.xeb_default_opts()
+    plan = B.xeb_plan_create(circ, bits, opts=o, open_qubits=open_q)
+    try:
+        st = B.xeb_plan_stats(plan)
+        root = B.xeb_plan_node(plan, st["n_nodes"] - 1)
+        assert root["n_legs"] == 3
+        assert root["b"] - root["a"] == 12 - 3
+        fixed = {int(b) & ~mask for b in bits}
+        assert root["kv"] == len(fixed)
+    finally:
+        B.xeb_plan_destroy(plan)
+    # bond legs keep their ids, the open legs follow them; an open leg cannot be sliced
+    _, n_legs = B.xeb_network_info(circ)
+    with pytest.raises(B.XebError) as e:
+        B.xeb_plan_create(circ, bits, slices=[n_legs + 1], opts=o, open_qubits=open_q)
+    assert e.value.status == 1
+    p2 = B.xeb_plan_create(circ, bits, slices=[3], opts=o, open_qubits=open_q)   # a bond leg: fine
+    B.xeb_plan_destroy(p2)
+    with pytest.raises(B.XebError) as e:
+        B.xeb_plan_create(circ, bits, opts=o, open_qubits=list(range(12)))
+    assert e.value.status == 5
+    big = inputs.random_grid_circuit(4, 5, 2, 7)
+    with pytest.raises(B.XebError) as e:
+        B.xeb_plan_create(big, inputs.uniform_bitstrings(20, 10, 1), opts=o, open_qubits=list(range(17)))
+    assert e.value.status == 5
