@@ -128,6 +128,10 @@ typedef struct {
                              memo-level kernel, faster for K = 16 tiles);
                              [5] = local-search proposals in thousands
                              (0: 2000 per leaf);
+                             [6] = 1: keyed contractions (k_v > 1, 128+
+                             rows, 16 <= K, N <= 64) use the keyed tensor-core
+                             form by default (TF32x3 only; otherwise it is
+                             one of the forms xeb_plan_autotune times);
                              others 0 */
 } xeb_plan_opts;
 

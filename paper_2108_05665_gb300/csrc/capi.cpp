@@ -214,6 +214,29 @@ bool tc_grouped(const Analysis& an, const Op& op, const xebk::GemmDesc& d, xebk:
     return true;
 }
 
+// Keyed tensor-core form: C_u = A_uL(u) B_uR(u) for every key u with the
+// single-key tile rules (128-row tiles, 16 <= K, N <= 64), one group of
+// M / 128 tiles per key; gathered A rows, W^T of the key's B written into
+// tensor memory when a CTA's tiles move to the next key.
+bool tc_keyed(const Op& op, const xebk::GemmDesc& d, xebk::TcDesc& t) {
+    if (op.kv <= 1 || op.M < 128 || op.M % 128 != 0 || op.K < 16 || op.K > 64 || op.N < 16 || op.N > 64) return false;
+    Op o1 = op;
+    o1.kv = 1;
+    if (!tc_tile(o1, t, xebk::kTc2RowBits, true)) return false;
+    t.tma = 0;
+    t.grp = 1;
+    t.keyed = 1;
+    t.tpg = op.M >> xebk::kTc2RowBits;
+    t.n_groups = op.kv;
+    t.c_key = d.c_key;
+    t.a_key = d.a_key;
+    t.b_key = d.b_key;
+    t.uL = d.uL;
+    t.uR = d.uR;
+    t.gstart = nullptr;
+    return true;
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -1054,6 +1077,15 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
             g.tc.tma = 0;
         return !(ch == CH_TC2 && !g.tc.tma);   // CH_TC2 means the TMA form
     }
+    // keyed tensor-core form: an autotuner choice, or the default with
+    // opts.reserved[6] = 1 (on the 53-qubit plans, whose keyed contractions
+    // are mostly K = N = 16, it ran no faster than the SIMT kernels)
+    if (tc_ok && !smem_w && (ch == CH_TC2_GATHER || (ch == CH_AUTO && p->opts.reserved[6] == 1)) &&
+        tc_keyed(op, d, g.tc)) {
+        g.kernel = GK_TC2;
+        tc_common(false);
+        return true;
+    }
     if (tc_ok && ch != CH_AUTO) return false;
     if (tf32 && (ch == CH_GROUPED || (ch == CH_AUTO && p->opts.reserved[1] != 1 && p->opts.reserved[4] == 1)) &&
         tc_grouped(p->an, op, d, g.tc)) {
@@ -1259,10 +1291,12 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             const int row_bits = p->gemms[i].kernel == GK_TC2 ? xebk::kTc2RowBits : 7;
             // grouped memo-level form: the columns are a group's keys (N2/2 of them at most)
             const bool grp = p->gemms[i].kernel == GK_TC2 && t.grp;
+            const bool keyed = grp && t.keyed;   // keyed form: the op's own K x N per key
+            const bool mgrp = grp && !t.keyed;   // memo-level groups: keys as columns
             int lnp = 0;
             while ((2 << lnp) < t.N2) ++lnp;
-            const int64_t gN = grp ? t.N2 / 2 : g.N;
-            const int nbn_eff = grp ? lnp : g.nbn;
+            const int64_t gN = mgrp ? t.N2 / 2 : g.N;
+            const int nbn_eff = mgrp ? lnp : g.nbn;
             if (t.M != g.M || t.M % (int64_t(1) << row_bits) != 0 || t.K2 != 2 * g.K || t.N2 != 2 * gN ||
                 t.K2 % 32 != 0 || t.N2 % 32 != 0 || t.N2 > 128 || t.K2 > 128 || t.n_chunks * 32 != t.K2 ||
                 t.n_chunks > 4 || t.T != row_bits + 4 || (!grp && g.kv != 1) ||
@@ -1270,7 +1304,12 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 why = "tensor-core tile of node " + std::to_string(op.node);
                 return false;
             }
-            if (grp && (t.tma || (t.tpg << row_bits) != g.M || t.n_groups != g.n_groups || t.c_key != g.M ||
+            if (keyed && (t.tma || (t.tpg << row_bits) != g.M || t.n_groups != g.kv || t.c_key != g.c_key ||
+                          t.a_key != g.a_key || t.b_key != g.b_key || t.uL != g.uL || t.uR != g.uR)) {
+                why = "keyed tensor-core form of node " + std::to_string(op.node);
+                return false;
+            }
+            if (mgrp && (t.tma || (t.tpg << row_bits) != g.M || t.n_groups != g.n_groups || t.c_key != g.M ||
                         t.N2 / 2 < an.nodes[op.b_node].kv || t.n_groups != an.nodes[op.a_node].kv ||
                         xebk::memo_scratch_bytes(t.n_groups, g.kv, g.K, 8) > p->memo_bytes ||
                         !inside(op.c_buf, t.c_off, t.c_off + g.kv * t.c_key - 1))) {

@@ -132,6 +132,14 @@ struct TcDesc {
     int64_t tpg, n_groups, c_key, bpack_off;
     const int32_t* gstart;
     const int64_t* grp_a;
+    // (grouped instantiation) keyed mode: one group per key u of a keyed
+    // contraction C_u = A_uL(u) B_uR(u); A at a_off + uL[u] a_key, B at b_off +
+    // uR[u] b_key (W^T rewritten when the key changes), C at c_off + u c_key;
+    // each CTA takes a contiguous block of tiles
+    int keyed;
+    int64_t a_key, b_key;
+    const int32_t* uL;
+    const int32_t* uR;
 };
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 constexpr int kTc2RowBits = 7;               // tensor-memory variant: 128 state rows per tile

@@ -200,6 +200,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     Sm2* S = reinterpret_cast<Sm2*>(cst + kRows * kCStride);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = kGrp ? t.n_groups * t.tpg : t.M / kRows;
+    // tiles of this CTA: t_first, t_first + t_step, ... below t_end.  Keyed
+    // mode takes one contiguous block, so consecutive tiles mostly share their
+    // key and W^T is rewritten about once per key; the other modes take every
+    // gridDim.x-th tile.
+    const bool blocked = kGrp && t.keyed;
+    const int64_t per_cta = (n_tiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t_first = blocked ? int64_t(blockIdx.x) * per_cta : int64_t(blockIdx.x);
+    const int64_t t_end = blocked ? (t_first + per_cta < n_tiles ? t_first + per_cta : n_tiles) : n_tiles;
+    const int64_t t_step = blocked ? 1 : int64_t(gridDim.x);
+    const int64_t my_tiles = t_end > t_first ? (t_end - 1 - t_first) / t_step + 1 : 0;
     const int nch = t.n_chunks;
     if (tid == 0) {
         for (int s = 0; s < kRing; ++s) {
@@ -246,7 +256,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- TMA mode: split landed raw chunks into the operand ring ----------------
         // raw and operand stages are 1024-byte aligned, so the 128-byte swizzle
         // the TMA applied is the layout the MMA reads: the split is a linear copy
-        const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
         const int64_t total = my_tiles * nch;
         for (int64_t c = 0; c < total; ++c) {
             const int s1 = int(c % kRaw), s2 = int(c % kRing);
@@ -273,7 +282,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- TMA mode: one thread issues the box loads ----------------
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
-            const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
             const int64_t total = my_tiles * nch;
             const int nbox = kRows >> t.box_log2;
             const int brow = (1 << t.box_log2) * 128;  // bytes of one box in shared memory
@@ -283,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if ((tile >> i) & 1) y |= int64_t(1) << (t.ext_apos[i] - t.row_shift);
                 return y;
             };
-            int64_t tile = blockIdx.x, c = 0;
+            int64_t tile = t_first, c = 0;
             int cin = 0;
             int64_t y0 = ybase(tile);
             for (; c < total; ++c) {
@@ -295,8 +303,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tma_load_2d(dst + j * brow, &tmap, kChunk * cin, int(y0 + t.box_y[j]), &S->rfull[s]);
                 if (++cin == nch) {
                     cin = 0;
-                    tile += gridDim.x;
-                    y0 = tile < n_tiles ? ybase(tile) : 0;
+                    tile += t_step;
+                    y0 = tile < t_end ? ybase(tile) : 0;
                 }
             }
             // the CTA must not exit with copies in flight: wait (bounded) for the last ones
@@ -325,10 +333,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             off[j] = o;
             pos[j] = swz(uint32_t(r) * 128u + uint32_t(k) * 8u);
         }
-        const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
         const int64_t total = my_tiles * nch;
         // issue-side cursor (chunks are issued in order)
-        int64_t ld_tile = blockIdx.x;
+        int64_t ld_tile = t_first;
         int ld_c = 0;
         int64_t cg = -1, cga = 0;   // grouped mode: last group seen and its A offset
         auto tile_base = [&](int64_t tile) {
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tile -= g * t.tpg;
                 if (g != cg) {
                     cg = g;
-                    cga = t.grp_a[g];
+                    cga = t.keyed ? (t.uL ? int64_t(t.uL[g]) * t.a_key : 0) : t.grp_a[g];
                 }
                 b = cga;
             }
@@ -353,8 +360,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         _Pragma("unroll") for (int j = 0; j < kPerThread; ++j) buf[U][j] = __ldg(Arow + off[j]); \
         if (++ld_c == nch) {                                                               \
             ld_c = 0;                                                                      \
-            ld_tile += gridDim.x;                                                          \
-            Arow = arena + t.a_off + (ld_tile < n_tiles ? tile_base(ld_tile) : 0) + t.chunk_off[0]; \
+            ld_tile += t_step;                                                             \
+            Arow = arena + t.a_off + (ld_tile < t_end ? tile_base(ld_tile) : 0) + t.chunk_off[0]; \
         } else {                                                                           \
             Arow += t.chunk_off[ld_c] - t.chunk_off[ld_c - 1];                             \
         }                                                                                  \
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = bar_wait(&S->wready, 0, t.err, 12);
             fence_after();
             uint32_t it = 0, tc = 0;
-            for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++tc) {
+            for (int64_t tile = t_first; tile < t_end && ok; tile += t_step, ++tc) {
                 const uint32_t b = 0, ub = tc;  // one accumulator pair (TMEM is full)
                 if (!bar_wait(&S->tempty[b], (ub & 1) ^ 1, t.err, 13)) break;
                 fence_after();
@@ -441,9 +448,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float2* B = arena + t.b_off;
             if constexpr (kGrp) {
                 const int64_t g = tile / t.tpg;
-                const int64_t u0 = t.gstart[g];
-                live = np < 2 * (t.gstart[g + 1] - u0);
-                B = arena + t.bpack_off + u0 * (t.K2 / 2);
+                if (t.keyed) {   // key g's own B operand, all N columns
+                    B = arena + t.b_off + (t.uR ? int64_t(t.uR[g]) * t.b_key : 0);
+                } else {
+                    const int64_t u0 = t.gstart[g];
+                    live = np < 2 * (t.gstart[g + 1] - u0);
+                    B = arena + t.bpack_off + u0 * (t.K2 / 2);
+                }
             }
             int64_t noff = 0;
             if (live)
@@ -471,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         };
-        if (blockIdx.x < n_tiles) write_wt(blockIdx.x);
+        if (t_first < t_end) write_wt(t_first);
         fence_before();
         bar_arrive(&S->wready);
         uint32_t tc = 0, ep = 0;
@@ -535,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ++ep;
             return ok;
         };
-        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++tc) {
+        for (int64_t tile = t_first; tile < t_end; tile += t_step, ++tc) {
             const uint32_t b = 0, ub = tc;
             const bool got = bar_wait(&S->tfull[b], ub & 1, t.err, 16);
             if (!__all_sync(0xffffffffu, got)) break;
@@ -543,8 +554,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // grouped mode: the next tile of this CTA needs its group's W^T,
             // written after this tile's accumulators are read and before they
             // are released (the MMAs of this tile are complete by then)
-            const int64_t nxt = tile + gridDim.x;
-            const bool switch_w = kGrp && nxt < n_tiles && nxt / t.tpg != tile / t.tpg;
+            const int64_t nxt = tile + t_step;
+            const bool switch_w = kGrp && nxt < t_end && nxt / t.tpg != tile / t.tpg;
             // D^T: lane = output column np, column = tile row; tensor memory is
             // released for the next tile's MMAs once the last load has landed
             const uint32_t db = tmem + 256;
@@ -579,15 +590,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             if constexpr (kGrp) {
                 const int64_t g = tile / t.tpg;
                 mt = tile - g * t.tpg;
-                const int64_t u0 = t.gstart[g];
-                nk = int(t.gstart[g + 1] - u0);
-                cbase = u0 * t.c_key;
+                if (t.keyed) {   // key g's result block
+                    cbase = g * t.c_key;
+                } else {
+                    const int64_t u0 = t.gstart[g];
+                    nk = int(t.gstart[g + 1] - u0);
+                    cbase = u0 * t.c_key;
+                }
             }
             for (int i = 0; i < t.n_ext; ++i)
                 if ((mt >> i) & 1) cbase += int64_t(1) << t.ext_cpos[i];
             float2* C = arena + t.c_off + cbase;
             const float2* st2 = reinterpret_cast<const float2*>(cst);
-            if (e_active && !kGrp) {
+            if (e_active && (!kGrp || t.keyed)) {
                 for (int jm = 0; jm < nmid; ++jm) {
                     int64_t gm = gq;
                     int sm2 = sq;
