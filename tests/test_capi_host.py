@@ -246,3 +246,44 @@ def test_batched_plan_root_holds_the_open_legs(lib):
     with pytest.raises(B.XebError) as e:
         B.xeb_plan_create(big, inputs.uniform_bitstrings(20, 10, 1), opts=o, open_qubits=list(range(17)))
     assert e.value.status == 5
+
+
+def test_op_layout_lists_are_permutations(lib):
+    """xeb_plan_op_layout: for every contraction of a plan, the row and
+    summed bits of A, the summed and column bits of B, and the row and
+    column bits of C are each a permutation of that tensor's address bits,
+    and the bit counts match the node ranks (App. A: 2^(q+r) products of a
+    pairwise contraction, legs of dimension 2)."""
+    circ = inputs.random_grid_circuit(4, 5, 10, 515)
+    bits = inputs.uniform_bitstrings(20, 500, 616)
+    for prec in (B.XEB_PREC_FP32, B.XEB_PREC_TF32X3):
+        o = B.xeb_default_opts()
+        o.precision = prec
+        plan = B.xeb_plan_create(circ, bits, opts=o)
+        try:
+            n_leaves = len(B.xeb_network_leaves(circ)[0])
+            n_gemm = 0
+            i = 0
+            while True:
+                try:
+                    L = B.xeb_plan_op_layout(plan, i)
+                except B.XebError as e:
+                    assert e.status == 1
+                    break
+                i += 1
+                if L["kind"] != 2:
+                    continue
+                n_gemm += 1
+                ra = len(L["a_pos_m"]) + len(L["a_pos_k"])
+                rb = len(L["b_pos_k"]) + len(L["b_pos_n"])
+                rc = len(L["c_pos_m"]) + len(L["c_pos_n"])
+                assert sorted(L["a_pos_m"] + L["a_pos_k"]) == list(range(ra))
+                assert sorted(L["b_pos_k"] + L["b_pos_n"]) == list(range(rb))
+                assert sorted(L["c_pos_m"] + L["c_pos_n"]) == list(range(rc))
+                assert len(L["a_pos_k"]) == len(L["b_pos_k"])
+                assert len(L["c_pos_m"]) == len(L["a_pos_m"]) and len(L["c_pos_n"]) == len(L["b_pos_n"])
+                nd = B.xeb_plan_node(plan, L["node"] - n_leaves)
+                assert nd["n_legs"] == rc and nd["n_shared"] == len(L["a_pos_k"])
+            assert n_gemm == n_leaves - 1
+        finally:
+            B.xeb_plan_destroy(plan)
