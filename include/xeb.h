@@ -263,6 +263,26 @@ xeb_status xeb_fidelity(struct xeb_plan_s* plan, double* F, double* mean_2np,
 xeb_status xeb_run(struct xeb_plan_s* plan, const uint64_t* bitstrings_host, size_t k,
                    double* amps_host, double* F_host, uintptr_t stream);
 
+/* Streamed evaluation for bitstring sets whose key tables and arena would
+ * not fit at once, in the lexicographic order of Alg. 4.  Without a tree the
+ * planner plans the first min(chunk, k) input bitstrings (a sample of the
+ * set); the bitstrings are then sorted by their bits read in that tree's bit
+ * order pi (first bit most significant), so neighbours share the longest key
+ * prefixes, and evaluated `chunk` at a time with the same tree and slices
+ * (slices NULL: the planner's, chosen on the sample).  The library allocates
+ * one workspace, grown to the largest chunk's xeb_plan_device_bytes, and
+ * frees it before returning; memory scales with the chunk, not with k.  A key
+ * prefix shared by two chunks is contracted once in each.  Outputs (host,
+ * each may be NULL): amps_host [2*k doubles] in input order, and over all k
+ * bitstrings F, the mean of 2^n p and the mean of (2^n p)^2 (Eq. 1).
+ * XEB_EINVAL for k = 0, chunk = 0 or a NULL bitstring pointer;
+ * XEB_EUNSUPPORTED for chunk above 2^24; errors of xeb_plan_create and
+ * xeb_run otherwise.  Synchronises `stream`. */
+xeb_status xeb_run_chunked(const xeb_circuit* circuit, const uint64_t* bitstrings_host, size_t k,
+                           const xeb_tree* tree, const xeb_slices* slices, const xeb_plan_opts* opts,
+                           size_t chunk, double* amps_host, double* F_host, double* mean_2np_host,
+                           double* mean_2np_sq_host, uintptr_t stream);
+
 /* Copy node `node`'s device key tables to host (for checks): key_of_bitstring
  * [k] int32, uL [k_v], uR [k_v] int32 (any may be NULL).  Synchronises. */
 xeb_status xeb_plan_keys(struct xeb_plan_s* plan, int node, int32_t* key_of_bitstring,

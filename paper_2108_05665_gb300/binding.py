@@ -120,6 +120,9 @@ _PROTOS = {
     "xeb_plan_create_batched": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _u64p, ctypes.c_size_t, ctypes.c_uint64,
                                                ctypes.POINTER(xeb_tree), ctypes.POINTER(xeb_slices),
                                                ctypes.POINTER(xeb_plan_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "xeb_run_chunked": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _u64p, ctypes.c_size_t, ctypes.POINTER(xeb_tree),
+                                       ctypes.POINTER(xeb_slices), ctypes.POINTER(xeb_plan_opts), ctypes.c_size_t,
+                                       _dblp, _dblp, _dblp, _dblp, ctypes.c_void_p]),
     "xeb_plan_op_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, ctypes.c_int, _i32p]),
     "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
                                             ctypes.POINTER(ctypes.c_int32)]),
@@ -297,6 +300,30 @@ def xeb_plan_op_layout(plan, op_index: int):
         out[name] = v[pos:pos + ln]
         pos += ln
     return out
+
+
+def xeb_run_chunked(circuit, bitstrings, chunk: int, tree=None, slices=None, opts=None, stream: int = 0):
+    """Streamed evaluation in Alg. 4's order, `chunk` bitstrings at a time;
+    returns (amplitudes complex128 [k] in input order, F, mean 2^n p,
+    mean (2^n p)^2)."""
+    ca = CircuitArrays(circuit)
+    bs = np.ascontiguousarray(bitstrings, dtype=np.uint64)
+    tp = sp = None
+    if tree is not None:
+        chl = np.ascontiguousarray(np.asarray(tree, dtype=np.int32).reshape(-1))
+        t = xeb_tree(len(chl) // 2, _ptr(chl, ctypes.c_int32))
+        tp = ctypes.byref(t)
+    if slices is not None:
+        sl = np.ascontiguousarray(np.asarray(slices, dtype=np.int32))
+        s = xeb_slices(len(sl), _ptr(sl, ctypes.c_int32))
+        sp = ctypes.byref(s)
+    amps = np.zeros(2 * len(bs), dtype=np.float64)
+    F, m1, m2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().xeb_run_chunked(ctypes.byref(ca.c), _ptr(bs, ctypes.c_uint64), len(bs), tp, sp,
+                                  ctypes.byref(opts) if opts is not None else None, chunk,
+                                  amps.ctypes.data_as(_dblp), ctypes.byref(F), ctypes.byref(m1), ctypes.byref(m2),
+                                  ctypes.c_void_p(stream or None)))
+    return amps.view(np.complex128), F.value, m1.value, m2.value
 
 
 def xeb_set_slice_subset(plan, frac: float, seed: int) -> int:

@@ -1725,6 +1725,96 @@ extern "C" xeb_status xeb_fidelity(xeb_plan_s* p, double* F, double* m1, double*
     return XEB_OK;
 }
 
+// Streamed evaluation in the lexicographic order of Alg. 4: the bitstrings
+// are sorted by their bits read in the tree's order pi (first bit most
+// significant), so consecutive ones share the longest key prefixes, and are
+// evaluated `chunk` at a time with one tree and slice set; every chunk's
+// plan binds the same library workspace, grown to the largest chunk's need.
+// The key tables and the arena then scale with the chunk, not with k.  A
+// prefix that straddles two chunks is contracted once in each.
+extern "C" xeb_status xeb_run_chunked(const xeb_circuit* circuit, const uint64_t* bits_host, size_t k,
+                                      const xeb_tree* tree, const xeb_slices* slices, const xeb_plan_opts* opts,
+                                      size_t chunk, double* amps_host, double* F_host, double* mean_2np_host,
+                                      double* mean_2np_sq_host, uintptr_t stream) {
+    if (!bits_host || k == 0) return fail(XEB_EINVAL, "need k >= 1 bitstrings");
+    if (chunk == 0) return fail(XEB_EINVAL, "chunk must be >= 1");
+    if (chunk > size_t(xebk::kMaxK)) return fail(XEB_EUNSUPPORTED, "chunk above the per-plan bitstring limit");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    xeb_plan_opts o;
+    if (opts) o = *opts;
+    else xeb_default_opts(&o);
+    o.reserved[2] = 1;   // each chunk's plan runs once: launch kernel by kernel, no graph capture
+    // the tree and slices: given, or planned on the first `chunk` input
+    // bitstrings (a sample of the set; the sorted order would skew it)
+    xeb_plan_s* first = nullptr;
+    const size_t k0 = std::min(chunk, k);
+    xeb_status s = create_plan(circuit, bits_host, k0, 0, tree, slices, &o, &first);
+    if (s != XEB_OK) return s;
+    std::unique_ptr<xeb_plan_s, void (*)(xeb_plan_s*)> hold(first, xeb_plan_destroy);
+    std::vector<int32_t> ch;
+    for (const auto& pr : first->tree) { ch.push_back(pr[0]); ch.push_back(pr[1]); }
+    const xeb_tree t_use{int(first->tree.size()), ch.data()};
+    const std::vector<int32_t> sl(first->sliced.begin(), first->sliced.end());
+    const xeb_slices s_use{int(sl.size()), sl.empty() ? nullptr : sl.data()};
+    const std::vector<int> pi = first->an.pi;
+    hold.reset();
+    // Alg. 4 order: ascending key over the bits in pi order
+    auto key_of = [&](uint64_t b) {
+        uint64_t key = 0;
+        for (int q : pi) key = (key << 1) | ((b >> q) & 1);
+        return key;
+    };
+    std::vector<std::pair<uint64_t, uint32_t>> order(k);
+    for (size_t i = 0; i < k; ++i) order[i] = {key_of(bits_host[i]), uint32_t(i)};
+    std::stable_sort(order.begin(), order.end(),
+                     [](const auto& x, const auto& y) { return x.first < y.first; });
+    std::vector<uint64_t> cb(std::min(chunk, k));
+    std::vector<double> ca(2 * std::min(chunk, k));
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    double sum_p = 0.0, sum_p2 = 0.0;   // of 2^n p and (2^n p)^2 over all k
+    s = XEB_OK;
+    for (size_t c0 = 0; c0 < k && s == XEB_OK; c0 += chunk) {
+        const size_t kc = std::min(chunk, k - c0);
+        for (size_t j = 0; j < kc; ++j) cb[j] = bits_host[order[c0 + j].second];
+        xeb_plan_s* pc = nullptr;
+        s = create_plan(circuit, cb.data(), kc, 0, &t_use, &s_use, &o, &pc);
+        if (s != XEB_OK) break;
+        std::unique_ptr<xeb_plan_s, void (*)(xeb_plan_s*)> hc(pc, xeb_plan_destroy);
+        const size_t need = xeb_plan_device_bytes(pc);
+        if (need > ws_bytes) {
+            if (ws) cudaFree(ws);
+            ws = nullptr;
+            ws_bytes = 0;
+            const cudaError_t e = cudaMalloc(&ws, need);
+            if (e != cudaSuccess) { s = fail(XEB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); break; }
+            ws_bytes = need;
+        }
+        s = xeb_plan_bind(pc, ws, ws_bytes, stream);
+        double m1 = 0, m2 = 0;
+        if (s == XEB_OK) s = xeb_run(pc, cb.data(), kc, ca.data(), nullptr, stream);
+        if (s == XEB_OK) s = xeb_fidelity(pc, nullptr, &m1, &m2, stream);
+        if (s != XEB_OK) break;
+        sum_p += m1 * double(kc);
+        sum_p2 += m2 * double(kc);
+        if (amps_host)
+            for (size_t j = 0; j < kc; ++j) {
+                const size_t i = order[c0 + j].second;
+                amps_host[2 * i] = ca[2 * j];
+                amps_host[2 * i + 1] = ca[2 * j + 1];
+            }
+    }
+    if (ws) {
+        cudaStreamSynchronize(st);
+        cudaFree(ws);
+    }
+    if (s != XEB_OK) return s;
+    if (F_host) *F_host = sum_p / double(k) - 1.0;
+    if (mean_2np_host) *mean_2np_host = sum_p / double(k);
+    if (mean_2np_sq_host) *mean_2np_sq_host = sum_p2 / double(k);
+    return XEB_OK;
+}
+
 extern "C" xeb_status xeb_run(xeb_plan_s* p, const uint64_t* bits_host, size_t k, double* amps_host, double* F,
                               uintptr_t stream) {
     xeb_status s = check_bound(p);

@@ -287,3 +287,14 @@ def test_op_layout_lists_are_permutations(lib):
             assert n_gemm == n_leaves - 1
         finally:
             B.xeb_plan_destroy(plan)
+
+
+def test_chunked_run_rejects_bad_arguments(lib):
+    circ = inputs.random_grid_circuit(3, 4, 8, 1)
+    bits = inputs.uniform_bitstrings(12, 50, 2)
+    with pytest.raises(B.XebError) as e:
+        B.xeb_run_chunked(circ, bits, 0)
+    assert e.value.status == 1
+    with pytest.raises(B.XebError) as e:
+        B.xeb_run_chunked(circ, bits[:0], 10)
+    assert e.value.status == 1
