@@ -368,7 +368,8 @@ def main():
         peak = hbm
         peak_note = "measured copy bandwidth (" + pk_kind + ")"
     traffic = tc_traffic_per_launch(d["bytes"] / d["launches"]) if name == "gemm_tc" else None
-    eff_tflops = st["flops_per_slice"] * n_run * args.steps * world / (ms_total / 1e3) / 1e12
+    step_flops, _ = B.xeb_plan_step_flops(plan.handle)   # launched work per step (cross-slice reuse counted)
+    eff_tflops = step_flops * args.steps * world / (ms_total / 1e3) / 1e12
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
@@ -390,7 +391,8 @@ def main():
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
                    "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},
         "complex_tflops": eff_tflops,
-        "flops_per_step": st["flops_per_slice"] * n_run,
+        "flops_per_step": step_flops,
+        "nodes_kept_across_slices": st["n_reused"],
         "memo_gain": st["single_amp_flops"] / max(st["flops_per_slice"], 1.0),
         "F": F if frac >= 1.0 else None, "F_e2e": Fe if frac >= 1.0 else None,
         "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": 8 * k,

@@ -115,7 +115,7 @@ typedef struct {
     uint64_t mem_budget;  /* M_max in bytes for the contraction arena            */
     uint64_t seed;        /* planner randomisation                               */
     int greedy_trials;    /* randomised greedy restarts                          */
-    int reserved[7];      /* [0] = 1: permute operands into [free][summed] blocks
+    int reserved[8];      /* [0] = 1: permute operands into [free][summed] blocks
                              before each contraction instead of gathering them in
                              place; [1] = 1: tensor-core kernel with the split B
                              in shared memory instead of B^T in tensor memory;
@@ -132,6 +132,8 @@ typedef struct {
                              rows, 16 <= K, N <= 64) use the keyed tensor-core
                              form by default (TF32x3 only; otherwise it is
                              one of the forms xeb_plan_autotune times);
+                             [7] = 1: no cross-slice reuse (every contraction
+                             runs in every slice; see xeb_plan_step_flops);
                              others 0 */
 } xeb_plan_opts;
 
@@ -152,7 +154,8 @@ typedef struct {
     int planner_used;
     int n_tc_launches;          /* tensor-core contractions per slice (after bind) */
     int n_tc_tma;               /* ... of which load A with TMA boxes             */
-    int reserved[3];
+    int reserved[3];            /* [0]: nodes whose result is kept across slices
+                                   (cross-slice reuse, see xeb_plan_step_flops) */
 } xeb_stats;
 
 /* Default options (FP32, AUTO planner, 64 GiB budget). */
@@ -323,6 +326,17 @@ xeb_status xeb_plan_profile(struct xeb_plan_s* plan, int enable);
  * *n_ops receives n.  Synchronises on the recorded events. */
 xeb_status xeb_plan_profile_ops(struct xeb_plan_s* plan, int cap, double* ms, double* launches, int32_t* cls,
                                 double* shape, int32_t* n_ops);
+
+/* Work of one xeb_amplitudes step over the slices it runs (all, or the
+ * subset of xeb_set_slice_subset), with cross-slice reuse: a node whose
+ * subtree holds sliced legs S_v is contracted only in the slices where a leg
+ * of S_v (or, for a node recomputed with its parent, of the parent's set)
+ * changed value from the previous slice, so slice-invariant subtrees run once
+ * (the sharing of common subexpressions across slices that the paper's
+ * introduction cites, applied to the slice loop of App. A "Slicing").  Writes
+ * the algorithmic flops (8 per complex multiply-add) and the number of
+ * contractions launched per step; either pointer may be NULL.  Host only. */
+xeb_status xeb_plan_step_flops(const struct xeb_plan_s* plan, double* flops, double* contractions);
 
 /* Operand and result addressing of step `op_index` of the plan's contraction
  * program (host only; the program of App. A/C's tree, one step per

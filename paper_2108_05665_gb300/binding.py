@@ -56,7 +56,7 @@ class xeb_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("planner", ctypes.c_int), ("block_qubits", ctypes.c_int),
                 ("group_leaves", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("mem_budget", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("greedy_trials", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("reserved", ctypes.c_int * 8)]
 
 
 class xeb_stats(ctypes.Structure):
@@ -71,7 +71,9 @@ class xeb_stats(ctypes.Structure):
                 ("reserved", ctypes.c_int * 3)]
 
     def as_dict(self):
-        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
+        d = {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
+        d["n_reused"] = self.reserved[0]   # nodes kept across slices (cross-slice reuse)
+        return d
 
 
 _PROTOS = {
@@ -123,6 +125,7 @@ _PROTOS = {
     "xeb_run_chunked": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _u64p, ctypes.c_size_t, ctypes.POINTER(xeb_tree),
                                        ctypes.POINTER(xeb_slices), ctypes.POINTER(xeb_plan_opts), ctypes.c_size_t,
                                        _dblp, _dblp, _dblp, _dblp, ctypes.c_void_p]),
+    "xeb_plan_step_flops": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp]),
     "xeb_plan_op_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, ctypes.c_int, _i32p]),
     "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
                                             ctypes.POINTER(ctypes.c_int32)]),
@@ -300,6 +303,13 @@ def xeb_plan_op_layout(plan, op_index: int):
         out[name] = v[pos:pos + ln]
         pos += ln
     return out
+
+
+def xeb_plan_step_flops(plan):
+    """(flops, contractions) one xeb_amplitudes step launches, with cross-slice reuse."""
+    fl, nc = ctypes.c_double(), ctypes.c_double()
+    _check(load().xeb_plan_step_flops(plan, ctypes.byref(fl), ctypes.byref(nc)))
+    return fl.value, nc.value
 
 
 def xeb_run_chunked(circuit, bitstrings, chunk: int, tree=None, slices=None, opts=None, stream: int = 0):

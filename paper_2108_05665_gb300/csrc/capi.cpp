@@ -313,6 +313,10 @@ struct xeb_plan_s {
     Network net;
     int w = 0;               // open qubits (multi-batch): 2^w amplitudes per bitstring
     xebk::RootMap rootmap{};  // where open-qubit bit j sits in the root's per-key block
+    // cross-slice reuse: a node is contracted in a slice only if a slice bit
+    // in node_mask[v] changed since the previous slice (all ones: always)
+    std::vector<uint32_t> node_mask;
+    int n_reused = 0;         // nodes whose result is kept across slices
     Tree tree;
     std::vector<int> sliced;
     Analysis an;
@@ -682,6 +686,56 @@ void plan_features(const Candidate& c, size_t n_sliced, const xeb_plan_opts& o, 
 }  // namespace
 
 namespace {
+// Cross-slice reuse.  A node's tensor depends on the slice value only through
+// the sliced legs of its subtree (m_v, a mask of slice bits).  Going down from
+// the root, a child keeps its own mask where it is strictly smaller than its
+// parent's effective mask e (so it can be skipped while the parent is
+// recomputed, and its buffer stays reserved for the whole step), else takes
+// the parent's (it is recomputed with the parent, its buffer lives as usual).
+// In slice t a node is contracted iff t = 0 or (s_t ^ s_{t-1}) & e_v != 0.
+// Off when the reserved buffers would push the arena above the plan's budget
+// (or above its own arena if that is larger), in permute-first mode, or with
+// opts.reserved[7] = 1.
+void setup_reuse(xeb_plan_s* p) {
+    const Analysis& an = p->an;
+    const int N = int(an.nodes.size()), L = an.L, S = int(p->sliced.size());
+    const uint32_t all = S >= 32 ? ~0u : (1u << S) - 1;
+    p->node_mask.assign(size_t(N), ~0u);
+    p->n_reused = 0;
+    if (S == 0 || p->opts.reserved[7] == 1 || p->opts.reserved[0] == 1) return;
+    std::vector<uint32_t> m(size_t(N), 0);
+    for (int j = 0; j < L; ++j)
+        for (int l : p->net.leaves[size_t(j)].legs) {
+            const auto it = std::find(p->sliced.begin(), p->sliced.end(), l);
+            if (it != p->sliced.end()) m[size_t(j)] |= 1u << int(it - p->sliced.begin());
+        }
+    for (int v = L; v < N; ++v) m[size_t(v)] = m[size_t(an.nodes[size_t(v)].l)] | m[size_t(an.nodes[size_t(v)].r)];
+    std::vector<uint32_t> e(size_t(N), all);
+    std::vector<int> keep;
+    for (int v = N - 1; v >= L; --v)
+        for (int c : {an.nodes[size_t(v)].l, an.nodes[size_t(v)].r}) {
+            if (m[size_t(c)] != e[size_t(v)] && c >= L) {
+                e[size_t(c)] = m[size_t(c)];
+                keep.push_back(c);
+            } else {
+                e[size_t(c)] = e[size_t(v)];
+            }
+        }
+    if (keep.empty()) return;
+    Program pr = p->prog;
+    for (int c : keep) {
+        Buffer& b = pr.bufs[size_t(pr.node_buf[size_t(c)])];
+        b.first = 0;
+        b.last = int(pr.ops.size()) + 1;
+    }
+    plan_memory(pr);
+    const double cap = std::max(double(p->opts.mem_budget), double(p->prog.arena_elems) * double(p->elem));
+    if (double(pr.arena_elems) * double(p->elem) > cap) return;
+    p->prog = std::move(pr);
+    for (int v = 0; v < N; ++v) p->node_mask[size_t(v)] = e[size_t(v)];
+    p->n_reused = int(keep.size());
+}
+
 xeb_status create_plan(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k, uint64_t open_mask,
                        const xeb_tree* tree, const xeb_slices* slices, const xeb_plan_opts* opts, xeb_plan_s** out) {
     if (!out) return fail(XEB_EINVAL, "out is NULL");
@@ -802,6 +856,7 @@ xeb_status create_plan(const xeb_circuit* circuit, const uint64_t* bitstrings, s
             p->rootmap.pos[j] = int8_t(int(lay.size()) - 1 - at);
         }
     }
+    setup_reuse(p.get());
     *out = p.release();
     return XEB_OK;
 }
@@ -901,6 +956,7 @@ extern "C" xeb_status xeb_plan_stats(xeb_plan_s* p, xeb_stats* s) {
         else ++s->n_permute_ops;
     }
     s->planner_used = p->planner_used;
+    s->reserved[0] = p->n_reused;
     for (size_t i = 0; i < p->gemms.size() && i < p->prog.ops.size(); ++i)
         if (const GemmLaunch& g = p->gemms[i];
             p->prog.ops[i].kind != OP_PERM && (g.kernel == GK_TC || g.kernel == GK_TC2)) {
@@ -1427,8 +1483,11 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
     const int64_t n_run = p->slice_ids.empty() ? int64_t(1) << p->sliced.size() : int64_t(p->slice_ids.size());
     const auto* ldesc = reinterpret_cast<const xebk::LeafDesc*>(tables + p->t_leaf_desc);
     const double es = double(sizeof(T));
+    int64_t s_prev = 0;
     for (int64_t si = 0; si < n_run; ++si) {
         const int64_t s = p->slice_ids.empty() ? si : p->slice_ids[size_t(si)];
+        const uint32_t changed = uint32_t(s ^ s_prev);   // slice bits that moved (unused for si = 0)
+        s_prev = s;
         {
             ProfScope ps(p, st, XEB_KC_LEAVES, 0.0, 0.0);
             XEB_CUDA(xebk::launch_leaves<T>(ldesc, an.L, leafdata, arena, tables, s, st));
@@ -1440,6 +1499,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 XEB_CUDA(xebk::launch_permute<T>(p->perms[i], arena + pr.bufs[op.src_buf].off,
                                                  arena + pr.bufs[op.dst_buf].off, st));
             } else {
+                if (si > 0 && !(changed & p->node_mask[size_t(op.node)])) continue;   // still holds this slice's value
                 const GemmLaunch& g = p->gemms[i];
                 const double ka = double(an.nodes[op.a_node].kv), kb = double(an.nodes[op.b_node].kv);
                 const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
@@ -1932,6 +1992,35 @@ extern "C" xeb_status xeb_plan_profile(xeb_plan_s* p, int enable) {
     p->op_ms.clear();
     p->op_n.clear();
     p->profiling = enable != 0;
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_step_flops(const xeb_plan_s* p, double* flops, double* contractions) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    const int S = int(p->sliced.size());
+    const int64_t n_run = p->slice_ids.empty() ? int64_t(1) << S : int64_t(p->slice_ids.size());
+    double fl = 0, nc = 0;
+    for (const Op& op : p->prog.ops) {
+        if (op.kind != OP_GEMM) continue;
+        const uint32_t e = p->node_mask[size_t(op.node)];
+        double times = 0;
+        if (p->slice_ids.empty()) {   // counting order: bit b moves every 2^b slices
+            int low = 0;
+            while (low < S && !((e >> low) & 1)) ++low;
+            times = low >= S ? 1.0 : std::ldexp(1.0, S - low);
+        } else {
+            int64_t prev = 0;
+            for (int64_t si = 0; si < n_run; ++si) {
+                const int64_t s = p->slice_ids[size_t(si)];
+                if (si == 0 || (uint32_t(s ^ prev) & e)) times += 1;
+                prev = s;
+            }
+        }
+        fl += times * 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
+        nc += times;
+    }
+    if (flops) *flops = fl;
+    if (contractions) *contractions = nc;
     return XEB_OK;
 }
 

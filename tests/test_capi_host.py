@@ -298,3 +298,65 @@ def test_chunked_run_rejects_bad_arguments(lib):
     with pytest.raises(B.XebError) as e:
         B.xeb_run_chunked(circ, bits[:0], 10)
     assert e.value.status == 1
+
+
+def _reuse_launches(plan, circ, ids):
+    """Contractions one step launches under the cross-slice rule, walked in
+    plain Python: masks of slice bits per subtree, effective masks top-down,
+    a node runs in slice t iff t = 0 or (s_t ^ s_{t-1}) & e_v != 0."""
+    tree, sliced = B.xeb_plan_tree(plan)
+    _, legs = B.xeb_network_leaves(circ)
+    L = len(legs)
+    m = [sum(1 << sliced.index(l) for l in legs[j] if l in sliced) for j in range(L)]
+    kids = []
+    for a, b in tree:
+        ca = -1 - a if a < 0 else L + a
+        cb = -1 - b if b < 0 else L + b
+        kids.append((ca, cb))
+        m.append(m[ca] | m[cb])
+    e = [0] * len(m)
+    e[-1] = (1 << len(sliced)) - 1
+    for v in range(len(m) - 1, L - 1, -1):
+        for c in kids[v - L]:
+            e[c] = m[c] if (m[c] != e[v] and c >= L) else e[v]
+    n = 0
+    for v in range(L, len(m)):
+        prev = None
+        for s in ids:
+            if prev is None or ((s ^ prev) & e[v]):
+                n += 1
+            prev = s
+    return n
+
+
+def test_cross_slice_reuse_counts(lib):
+    """Slice-invariant and partly invariant subtrees run once per value of
+    the sliced legs they hold: the step's work with reuse is below the plain
+    sum over slices, equal to it with reuse off (opts.reserved[7] = 1), and
+    the count of launched contractions matches a plain walk of the rule, both
+    for all slices (closed form) and for a seeded subset (enumerated)."""
+    circ = inputs.random_grid_circuit(3, 4, 8, 4545)
+    bits = inputs.uniform_bitstrings(12, 60, 4646)
+    net = network.fused_network(circ)
+    bonds = sorted({l for leaf in net.leaves for l in leaf.legs})
+    sliced = [bonds[3], bonds[17], bonds[40], bonds[55]]
+    res = {}
+    for off in (0, 1):
+        o = B.xeb_default_opts()
+        o.reserved[7] = off
+        plan = B.xeb_plan_create(circ, bits, slices=sliced, opts=o)
+        try:
+            st = B.xeb_plan_stats(plan)
+            fl, nc = B.xeb_plan_step_flops(plan)
+            ids = list(range(st["n_slices"]))
+            assert nc == _reuse_launches(plan, circ, ids) if off == 0 else nc == st["n_gemm_ops"] * st["n_slices"]
+            res[off] = (fl, nc, st["n_reused"], st["flops_per_slice"] * st["n_slices"])
+            if off == 0:
+                n_sub = B.xeb_set_slice_subset(plan, 0.5, 99)
+                sub = [int(x) for x in B.xeb_plan_slice_ids(plan, n_sub)]
+                fl2, nc2 = B.xeb_plan_step_flops(plan)
+                assert nc2 == _reuse_launches(plan, circ, sub)
+        finally:
+            B.xeb_plan_destroy(plan)
+    assert res[1][0] == res[1][3] and res[1][2] == 0
+    assert res[0][2] >= 1 and res[0][0] < res[0][3] and res[0][1] < res[1][1]

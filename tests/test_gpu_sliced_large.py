@@ -194,3 +194,39 @@ def test_grid6x9m1_split_precision_matches_fp64_on_gpu():
     # measured 1.0e-5 on a GB300: the per-amplitude target of 1e-5 is just
     # reached at this depth; the bound leaves room for that measurement only
     assert d.max() < 1.5e-5
+
+
+@pytest.mark.parametrize("precision", [B.XEB_PREC_FP32, B.XEB_PREC_TF32X3])
+def test_cross_slice_reuse_leaves_results_unchanged(precision):
+    """Subtrees whose sliced legs did not change value since the previous
+    slice keep their tensors instead of being contracted again; the full sum
+    and a seeded partial sum are the same as with every contraction run in
+    every slice (opts.reserved[7] = 1), and the full sum matches the FP64
+    state vector."""
+    from oracle import statevec
+    circ = inputs.random_grid_circuit(4, 5, 10, 5353)
+    bits = inputs.uniform_bitstrings(20, 400, 5454)
+    out = {}
+    for off in (0, 1):
+        o = B.xeb_default_opts()
+        o.precision = precision
+        o.planner = B.XEB_PLANNER_ANNEAL
+        o.mem_budget = 4 << 20                       # forces several sliced legs
+        o.reserved[7] = off
+        tree = slices = None
+        if off == 1:
+            tree, slices = out[0][3]
+        plan = B.Plan(circ, bits, tree=tree, slices=list(slices) if slices is not None else None, opts=o).bind()
+        st = plan.stats()
+        full, F, _ = _amps(plan, bits)
+        part, _, n_run = _amps(plan, bits, 0.5, 808)
+        out[off] = (full, part, st, plan.tree())
+        plan.close()
+    st0 = out[0][2]
+    print("reuse: %d sliced legs, %d nodes kept across slices" % (st0["n_sliced"], st0["n_reused"]))
+    assert st0["n_sliced"] >= 2 and out[1][2]["n_reused"] == 0
+    for a, b in ((out[0][0], out[1][0]), (out[0][1], out[1][1])):
+        scale = np.sqrt(np.mean(np.abs(b) ** 2))
+        assert np.abs(a - b).max() <= 1e-6 * scale
+    ref = statevec.amplitudes(circ, bits)
+    assert rel_err(out[0][0], ref, 20).max() < 1e-5
