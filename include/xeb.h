@@ -279,7 +279,7 @@ xeb_status xeb_run(struct xeb_plan_s* plan, const uint64_t* bitstrings_host, siz
  * each may be NULL): amps_host [2*k doubles] in input order, and over all k
  * bitstrings F, the mean of 2^n p and the mean of (2^n p)^2 (Eq. 1).
  * XEB_EINVAL for k = 0, chunk = 0 or a NULL bitstring pointer;
- * XEB_EUNSUPPORTED for chunk above 2^24; errors of xeb_plan_create and
+ * XEB_EUNSUPPORTED for chunk above 2^24 or k above 2^32 - 1; errors of xeb_plan_create and
  * xeb_run otherwise.  Synchronises `stream`. */
 xeb_status xeb_run_chunked(const xeb_circuit* circuit, const uint64_t* bitstrings_host, size_t k,
                            const xeb_tree* tree, const xeb_slices* slices, const xeb_plan_opts* opts,

@@ -1799,6 +1799,7 @@ extern "C" xeb_status xeb_run_chunked(const xeb_circuit* circuit, const uint64_t
     if (!bits_host || k == 0) return fail(XEB_EINVAL, "need k >= 1 bitstrings");
     if (chunk == 0) return fail(XEB_EINVAL, "chunk must be >= 1");
     if (chunk > size_t(xebk::kMaxK)) return fail(XEB_EUNSUPPORTED, "chunk above the per-plan bitstring limit");
+    if (k > size_t(UINT32_MAX)) return fail(XEB_EUNSUPPORTED, "more than 2^32 - 1 bitstrings");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     xeb_plan_opts o;
     if (opts) o = *opts;
