@@ -1155,6 +1155,9 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
     if (ch != CH_AUTO && ch != CH_SIMT) return false;
     if (stream_tile(op, p->elem, g.s))
         g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
+    // N = 1 with a deep sum over few rows: a warp per output (the GEMV kernel
+    // would run one long dependent chain per thread on a nearly idle GPU)
+    else if (op.N == 1 && op.K >= 128 && op.M <= 64) g.kernel = xebk::GK_TAIL;
     else if (op.N == 1) g.kernel = xebk::GK_GEMV;
     else if (op.K >= 32 && std::min(op.M, op.N) <= xebk::kKdTile && d.c_natural) g.kernel = xebk::GK_KDEEP;
     else if (op.M >= 16 && op.N >= 16) g.kernel = xebk::GK_TILED;

@@ -720,18 +720,22 @@ __global__ void k_gemm_gemv(const __grid_constant__ GemmDesc g, T* __restrict__ 
 // M == N == 1: a warp per key, lanes split K, shuffle reduction.
 template <typename T>
 __global__ void k_gemm_tail(const __grid_constant__ GemmDesc g, T* __restrict__ arena) {
+    // one warp per output (key u, row m) of an N = 1 contraction: lanes
+    // stride the summed index, a shuffle tree adds their partial sums
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t u = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; u < g.kv; u += warps) {
+    const int64_t total = g.kv * g.M;
+    for (int64_t w = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; w < total; w += warps) {
+        const int64_t u = w / g.M, m = w - u * g.M;
         const int64_t ua = g.uL ? g.uL[u] : 0;
         const int64_t ub = g.uR ? g.uR[u] : 0;
-        const T* a = arena + g.a_off + ua * g.a_key;
+        const T* a = arena + g.a_off + ua * g.a_key + scatter(m, g.apm, g.nam);
         const T* b = arena + g.b_off + ub * g.b_key;
         T acc = czero<T>();
         for (int64_t k = lane; k < g.K; k += 32)
             acc = cfma(acc, a[scatter(k, g.apk, g.nak)], b[scatter(k, g.bpk, g.nbk)]);
         for (int d = 16; d > 0; d >>= 1) acc = cadd(acc, shfl_down(acc, d));
-        if (lane == 0) arena[g.c_off + u * g.c_key] = acc;
+        if (lane == 0) arena[g.c_off + u * g.c_key + m] = acc;
     }
 }
 
@@ -753,7 +757,7 @@ cudaError_t launch_gemm(int kernel, const GemmDesc& g, T* arena, cudaStream_t st
             break;
         }
         case GK_TAIL:
-            k_gemm_tail<T><<<grid_for(g.kv * 32, 256, cap), 256, 0, st>>>(g, arena);
+            k_gemm_tail<T><<<grid_for(g.kv * g.M * 32, 256, cap), 256, 0, st>>>(g, arena);
             break;
         default:
             k_gemm_generic<T><<<grid_for(g.kv * g.M * g.N, 256, cap), 256, 0, st>>>(g, arena);

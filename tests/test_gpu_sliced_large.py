@@ -230,3 +230,23 @@ def test_cross_slice_reuse_leaves_results_unchanged(precision):
         assert np.abs(a - b).max() <= 1e-6 * scale
     ref = statevec.amplitudes(circ, bits)
     assert rel_err(out[0][0], ref, 20).max() < 1e-5
+
+
+def test_deep_sum_few_rows_contraction_matches_statevec():
+    """An annealed, sliced 3x6-grid plan whose tree holds an N = 1
+    contraction with a deep sum over few rows (M = 4, K = 128): it runs one
+    warp per output; the amplitudes match the FP64 state vector."""
+    from oracle import statevec
+    circ = inputs.random_grid_circuit(3, 6, 12, 12)
+    bits = inputs.uniform_bitstrings(18, 300, 13)
+    o = B.xeb_default_opts()
+    o.planner = B.XEB_PLANNER_ANNEAL
+    o.mem_budget = 4 << 20
+    from gpu_util import run
+    amps, F, plan = run(circ, bits, precision=B.XEB_PREC_FP32, opts=o)
+    print({k: (round(v["ms"], 3), v["launches"]) for k, v in plan.profile.items()})
+    assert "gemm_tail" in plan.profile
+    ref = statevec.amplitudes(circ, bits)
+    assert rel_err(amps, ref, 18).max() < 1e-5
+    assert abs(F - xeb.fidelity(ref, 18)) < 1e-6
+    plan.close()
