@@ -59,7 +59,7 @@ typedef enum {
     XEB_ENOMEM = 2,        /* device or host allocation failed / too small     */
     XEB_ECUDA = 3,         /* a CUDA runtime call failed                       */
     XEB_ETIMEOUT = 4,      /* a device-side bounded wait gave up               */
-    XEB_EUNSUPPORTED = 5,  /* valid request this build does not support        */
+    XEB_EUNSUPPORTED = 5,  /* valid request the library does not support       */
     XEB_ECANCELLED = 6,
     XEB_EDEVICE = 7        /* a device-side consistency check failed           */
 } xeb_status;
