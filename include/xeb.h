@@ -338,6 +338,15 @@ xeb_status xeb_plan_profile_ops(struct xeb_plan_s* plan, int cap, double* ms, do
  * contractions launched per step; either pointer may be NULL.  Host only. */
 xeb_status xeb_plan_step_flops(const struct xeb_plan_s* plan, double* flops, double* contractions);
 
+/* Per tree node v (leaves 0 .. n_leaves-1, then internal nodes in post-order;
+ * host only): the arena placement of its tensor from the emulation-mode
+ * allocator -- element offset off[v] and size elems[v] (complex elements) --
+ * and the cross-slice mask[v]: the slice bits whose change makes the node be
+ * contracted again (all ones without reuse).  Arrays of *n_nodes entries, any
+ * may be NULL; call with all NULL to read *n_nodes first. */
+xeb_status xeb_plan_buffers(const struct xeb_plan_s* plan, int64_t* off, int64_t* elems, uint32_t* mask,
+                            int32_t* n_nodes);
+
 /* Operand and result addressing of step `op_index` of the plan's contraction
  * program (host only; the program of App. A/C's tree, one step per
  * contraction or permutation).  Writes min(cap, n) int32 values to out (may be

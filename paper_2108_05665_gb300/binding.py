@@ -125,6 +125,7 @@ _PROTOS = {
     "xeb_run_chunked": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _u64p, ctypes.c_size_t, ctypes.POINTER(xeb_tree),
                                        ctypes.POINTER(xeb_slices), ctypes.POINTER(xeb_plan_opts), ctypes.c_size_t,
                                        _dblp, _dblp, _dblp, _dblp, ctypes.c_void_p]),
+    "xeb_plan_buffers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _i32p]),
     "xeb_plan_step_flops": (ctypes.c_int, [ctypes.c_void_p, _dblp, _dblp]),
     "xeb_plan_op_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, ctypes.c_int, _i32p]),
     "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
@@ -303,6 +304,18 @@ def xeb_plan_op_layout(plan, op_index: int):
         out[name] = v[pos:pos + ln]
         pos += ln
     return out
+
+
+def xeb_plan_buffers(plan):
+    """Per node: arena element offset, size, cross-slice mask (numpy arrays)."""
+    n = ctypes.c_int32()
+    _check(load().xeb_plan_buffers(plan, None, None, None, ctypes.byref(n)))
+    off = np.zeros(n.value, dtype=np.int64)
+    el = np.zeros(n.value, dtype=np.int64)
+    mk = np.zeros(n.value, dtype=np.uint32)
+    _check(load().xeb_plan_buffers(plan, off.ctypes.data_as(ctypes.c_void_p), el.ctypes.data_as(ctypes.c_void_p),
+                                   mk.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
+    return off, el, mk
 
 
 def xeb_plan_step_flops(plan):

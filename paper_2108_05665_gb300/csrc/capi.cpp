@@ -1999,6 +1999,20 @@ extern "C" xeb_status xeb_plan_profile(xeb_plan_s* p, int enable) {
     return XEB_OK;
 }
 
+extern "C" xeb_status xeb_plan_buffers(const xeb_plan_s* p, int64_t* off, int64_t* elems, uint32_t* mask,
+                                       int32_t* n_nodes) {
+    if (!p || !n_nodes) return fail(XEB_EINVAL, "NULL plan or n_nodes");
+    const int N = int(p->an.nodes.size());
+    *n_nodes = N;
+    for (int v = 0; v < N; ++v) {
+        const Buffer& b = p->prog.bufs[size_t(p->prog.node_buf[size_t(v)])];
+        if (off) off[v] = b.off;
+        if (elems) elems[v] = b.elems;
+        if (mask) mask[v] = p->node_mask[size_t(v)];
+    }
+    return XEB_OK;
+}
+
 extern "C" xeb_status xeb_plan_step_flops(const xeb_plan_s* p, double* flops, double* contractions) {
     if (!p) return fail(XEB_EINVAL, "NULL plan");
     const int S = int(p->sliced.size());

@@ -360,3 +360,86 @@ def test_cross_slice_reuse_counts(lib):
             B.xeb_plan_destroy(plan)
     assert res[1][0] == res[1][3] and res[1][2] == 0
     assert res[0][2] >= 1 and res[0][0] < res[0][3] and res[0][1] < res[1][1]
+
+
+def _replay_step(plan, circ, elem, ids):
+    """Replay one step's data flow over the plan's arena placement, slices in
+    the order ids: every slice rewrites the leaves and runs each contraction
+    whose cross-slice mask saw a change (all of them in the first slice); an
+    operand must still hold its node's value for the current slice (the
+    node's own sliced-leg bits).  Returns the number of stale operand reads
+    and the number of nodes kept across slices."""
+    off, el, mk = B.xeb_plan_buffers(plan)
+    st = B.xeb_plan_stats(plan)
+    tree, sliced = B.xeb_plan_tree(plan)
+    _, legs = B.xeb_network_leaves(circ)
+    L = len(legs)
+    m = [sum(1 << sliced.index(l) for l in legs[j] if l in sliced) for j in range(L)]
+    for a, b in tree:
+        m.append(m[-1 - a if a < 0 else L + a] | m[-1 - b if b < 0 else L + b])
+    ops, i = [], 0
+    while True:
+        try:
+            lay = B.xeb_plan_op_layout(plan, i)
+        except B.XebError:
+            break
+        i += 1
+        if lay["kind"] == 2:
+            ops.append((lay["node"], lay["a_node"], lay["b_node"]))
+    n_arena = st["arena_bytes"] // elem
+    owner = np.full(n_arena, -1, dtype=np.int32)
+    ver = np.zeros(n_arena, dtype=np.int64)
+
+    def holds(v, s):
+        sl = slice(off[v], off[v] + el[v])
+        return bool(np.all(owner[sl] == v) and np.all(ver[sl] == (s & m[v])))
+
+    def put(v, s):
+        sl = slice(off[v], off[v] + el[v])
+        owner[sl] = v
+        ver[sl] = s & m[v]
+
+    bad, prev = 0, None
+    for s in ids:
+        for j in range(L):
+            put(j, s)
+        for v, a, b in ops:
+            if prev is not None and not ((s ^ prev) & int(mk[v])):
+                continue
+            bad += (not holds(a, s)) + (not holds(b, s))
+            put(v, s)
+        bad += not holds(len(m) - 1, s)
+        prev = s
+    return bad, st["n_reused"]
+
+
+@pytest.mark.parametrize("case", ["given", "annealed", "batched", "subset"])
+def test_cross_slice_reuse_replay_reads_fresh_operands(lib, case):
+    """The arena placement with buffers kept across slices is consistent with
+    the skip rule: replaying a step's data flow (every slice in counting
+    order, or a shuffled seeded subset) finds no operand overwritten before
+    it is read."""
+    o = B.xeb_default_opts()
+    if case == "given":
+        circ = inputs.random_grid_circuit(3, 4, 8, 4545)
+        bits = inputs.uniform_bitstrings(12, 60, 4646)
+        net = network.fused_network(circ)
+        bonds = sorted({l for leaf in net.leaves for l in leaf.legs})
+        plan = B.xeb_plan_create(circ, bits, slices=[bonds[3], bonds[17], bonds[40], bonds[55]], opts=o)
+    else:
+        circ = inputs.random_grid_circuit(4, 5, 10, 5353)
+        bits = inputs.uniform_bitstrings(20, 400, 5454)
+        o.planner = B.XEB_PLANNER_ANNEAL
+        o.mem_budget = 4 << 20
+        plan = B.xeb_plan_create(circ, bits, opts=o, open_qubits=[2, 11, 17] if case == "batched" else None)
+    try:
+        frac, seed = (0.75, 2024) if case == "subset" else (1.0, 0)
+        n = B.xeb_set_slice_subset(plan, frac, seed)
+        ids = [int(x) for x in B.xeb_plan_slice_ids(plan, n)]
+        if case == "subset":
+            assert ids != sorted(ids)
+        bad, kept = _replay_step(plan, circ, 8, ids)
+        assert kept >= 1 and len(ids) >= 4
+        assert bad == 0
+    finally:
+        B.xeb_plan_destroy(plan)
