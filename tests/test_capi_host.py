@@ -443,3 +443,26 @@ def test_cross_slice_reuse_replay_reads_fresh_operands(lib, case):
         assert bad == 0
     finally:
         B.xeb_plan_destroy(plan)
+
+
+def test_new_entry_points_reject_bad_arguments(lib):
+    import ctypes as C
+    circ = inputs.random_grid_circuit(3, 4, 8, 77)
+    bits = inputs.uniform_bitstrings(12, 20, 78)
+    with pytest.raises(B.XebError) as e:        # open qubit outside the circuit
+        B.xeb_plan_create(circ, bits, open_qubits=[12])
+    assert e.value.status == 1
+    n = C.c_int32()
+    assert B.load().xeb_plan_buffers(None, None, None, None, C.byref(n)) == 1
+    assert B.load().xeb_plan_step_flops(None, None, None) == 1
+    assert B.load().xeb_plan_op_layout(None, 0, None, 0, C.byref(n)) == 1
+    plan = B.xeb_plan_create(circ, bits)
+    try:
+        assert B.load().xeb_plan_buffers(plan, None, None, None, None) == 1
+        with pytest.raises(B.XebError):
+            B.xeb_plan_op_layout(plan, -1)
+        off, el, mk = B.xeb_plan_buffers(plan)
+        assert len(off) == 2 * len(B.xeb_network_leaves(circ)[0]) - 1
+        assert np.all(el > 0) and np.all(off >= 0) and np.all(mk == 0xFFFFFFFF)   # unsliced: no reuse
+    finally:
+        B.xeb_plan_destroy(plan)
