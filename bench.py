@@ -208,8 +208,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="launch the step kernel by kernel instead of replaying one captured CUDA graph")
-    ap.add_argument("--tc-variant", default="tmem", choices=["tmem", "smem"],
-                    help="tensor-core kernel: B^T in tensor memory (default) or split B in shared memory")
+    ap.add_argument("--split-bits", type=int, default=0,
+                    help="tensor-core split: bits of the common-grid big parts (8..11; 0 = library default)")
+    ap.add_argument("--split-terms", type=int, default=0, choices=[0, 3, 4],
+                    help="tensor-core split: 3 or 4 products per term (0 = library default)")
     ap.add_argument("--planner", default="plain", choices=["plain", "learned", "anneal"],
                     help="plain: the planner's own objective; learned: the cost model's top candidates and the "
                          "plain plan are timed and the fastest kept (plan-time, outside the timed region); "
@@ -247,7 +249,8 @@ def main():
     prec = {"fp32": B.XEB_PREC_FP32, "tf32x3": B.XEB_PREC_TF32X3}[args.precision]
     o = B.xeb_default_opts()
     o.precision = prec
-    o.reserved[1] = 1 if args.tc_variant == "smem" else 0
+    o.split_bits = args.split_bits
+    o.split_terms = args.split_terms
     o.reserved[2] = 1 if args.eager else 0
     o.reserved[3] = 1 if args.tc_loads == "gather" else 0
     if args.planner == "anneal":
@@ -377,7 +380,8 @@ def main():
         "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32x3": "tf32x3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w.name, "desc": workload_desc(w), "precision": args.precision,
-                   "tc_variant": args.tc_variant, "tc_loads": args.tc_loads,
+                   "split": "bits %s, terms %s" % (args.split_bits or "default", args.split_terms or "default"),
+                   "tc_loads": args.tc_loads,
                    "autotune": ("%d reps per form, %d contractions changed form" % (args.autotune, tuned))
                    if tuned is not None else "off",
                    "launch": "kernel by kernel" if args.eager else "one CUDA graph per step",

@@ -117,8 +117,12 @@ typedef struct {
     int greedy_trials;    /* randomised greedy restarts                          */
     int reserved[8];      /* [0] = 1: permute operands into [free][summed] blocks
                              before each contraction instead of gathering them in
-                             place; [1] = 1: tensor-core kernel with the split B
-                             in shared memory instead of B^T in tensor memory;
+                             place; [1]: rounding of the leaves and folded
+                             constants of a complex64 plan: 0 keeps each
+                             tensor's norm (xeb_round_keep_norm), 1 rounds to
+                             nearest; an FP64 plan with 1 or 2 takes those
+                             complex64 values (the error the rounding alone
+                             causes);
                              [2] = 1: launch kernels one by one instead of
                              replaying one captured CUDA graph per step;
                              [3] = 1: tensor-core contractions gather A with
@@ -135,6 +139,28 @@ typedef struct {
                              [7] = 1: no cross-slice reuse (every contraction
                              runs in every slice; see xeb_plan_step_flops);
                              others 0 */
+    int split_bits;       /* XEB_PREC_TF32X3: bits of the big part of each
+                             operand, 8..11 (0 = 10).  Big parts of one state
+                             row of a K-chunk (32 real values) and of one row of
+                             W^T lie on a common grid of 2^-split_bits of that
+                             group's largest magnitude, so the big*big sums are
+                             exact in the FP32 accumulator (no truncation bias)
+                             while they stay below 2^24 grid units            */
+    int split_terms;      /* XEB_PREC_TF32X3: products per term, 3 (big*big,
+                             big*small, small*big) or 4 (+ small*small);
+                             0 = 4                                           */
+    uint32_t timeout_ms;  /* limit of every device-side wait of the
+                             tensor-core kernels (mbarrier hand-offs, copies);
+                             a wait that runs out sets the plan's error word
+                             and the call returns XEB_ETIMEOUT (0 = 2000)     */
+    int fold_legs;        /* constant folding: a subtree that depends on no
+                             output bit, sliced leg or open leg, and whose
+                             tensors have at most fold_legs legs, is contracted
+                             once on the host in FP64 when the plan is created
+                             and its result is uploaded at bind, rounded like
+                             the leaves (xeb_round_keep_norm); its leaves and
+                             contractions never run on the device.  0 = 16,
+                             -1 = no folding                                  */
 } xeb_plan_opts;
 
 typedef struct {
@@ -155,8 +181,24 @@ typedef struct {
     int n_tc_launches;          /* tensor-core contractions per slice (after bind) */
     int n_tc_tma;               /* ... of which load A with TMA boxes             */
     int reserved[3];            /* [0]: nodes whose result is kept across slices
-                                   (cross-slice reuse, see xeb_plan_step_flops) */
+                                   (cross-slice reuse, see xeb_plan_step_flops);
+                                   [1]: nodes evaluated on the host (constant
+                                   folding, opts.fold_legs), leaves included;
+                                   [2]: folded subtrees uploaded at bind      */
 } xeb_stats;
+
+/* Single-precision rounding that keeps the sum of squares (host only; the
+ * library rounds every leaf tensor of a complex64 plan with it, real and
+ * imaginary parts as 2m values).  x: host [n] doubles, y: host [n] floats
+ * (caller-owned).  Every y[i] is one of the two floats nearest x[i]: first the
+ * nearest, then, in order of increasing extra rounding error, a value moves
+ * to its other neighbour whenever that brings sum_i y_i^2 closer to sum_i
+ * x_i^2.  Why: the leaves are gate tensors (App. B, "leaf value tables")
+ * whose squared norm is fixed by unitarity; nearest rounding of the fused
+ * gates of these circuits shrinks it systematically, and the circuit's
+ * output norm with it (a shift of a few 1e-7 in F at 20-30 qubits).  NULL
+ * pointers: no effect. */
+void xeb_round_keep_norm(const double* x, size_t n, float* y);
 
 /* Default options (FP32, AUTO planner, 64 GiB budget). */
 void xeb_default_opts(xeb_plan_opts* opts);

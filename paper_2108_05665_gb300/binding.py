@@ -56,7 +56,8 @@ class xeb_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("planner", ctypes.c_int), ("block_qubits", ctypes.c_int),
                 ("group_leaves", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("mem_budget", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("greedy_trials", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("reserved", ctypes.c_int * 8), ("split_bits", ctypes.c_int), ("split_terms", ctypes.c_int),
+                ("timeout_ms", ctypes.c_uint32), ("fold_legs", ctypes.c_int)]
 
 
 class xeb_stats(ctypes.Structure):
@@ -73,11 +74,14 @@ class xeb_stats(ctypes.Structure):
     def as_dict(self):
         d = {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
         d["n_reused"] = self.reserved[0]   # nodes kept across slices (cross-slice reuse)
+        d["n_folded"] = self.reserved[1]   # nodes evaluated on the host (constant folding)
+        d["n_fold_roots"] = self.reserved[2]
         return d
 
 
 _PROTOS = {
     "xeb_default_opts": (None, [ctypes.POINTER(xeb_plan_opts)]),
+    "xeb_round_keep_norm": (None, [_dblp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_float)]),
     "xeb_network_info": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
     "xeb_network_leaves": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _i32p, _i32p]),
@@ -183,6 +187,13 @@ def xeb_default_opts() -> xeb_plan_opts:
     o = xeb_plan_opts()
     load().xeb_default_opts(ctypes.byref(o))
     return o
+
+
+def xeb_round_keep_norm(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(x.shape, dtype=np.float32)
+    load().xeb_round_keep_norm(x.ctypes.data_as(_dblp), x.size, y.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return y
 
 
 def xeb_network_info(circuit):

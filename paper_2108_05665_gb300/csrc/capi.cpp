@@ -39,11 +39,19 @@ namespace {
 
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-constexpr int GK_TC = 100;   // tcgen05 split-precision kernel, split W in smem (tc_gemm.cu)
 constexpr int GK_TC2 = 101;  // tcgen05 split-precision kernel, W^T in tensor memory (tc_gemm2.cu)
+// Defaults of the split-precision options (xeb_plan_opts.split_bits,
+// split_terms, timeout_ms): big parts of 10 bits on a common grid, four
+// products, 2 s per device-side wait.  With 11 bits the big*big sums of the
+// 30-qubit workload pass 2^24 grid units often enough to bias F by 1.3e-6;
+// with three products the missing small*small term (2^-20 of the grid)
+// costs 1.7e-5 per amplitude.
+constexpr int kSplitBitsDefault = 10;
+constexpr int kSplitTermsDefault = 4;
+constexpr uint32_t kTimeoutMsDefault = 2000;
 
 // kernel-form choices of a contraction (autotuner candidates)
-enum Choice { CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_TC1 = 2, CH_GROUPED = 3, CH_SIMT = 4, CH_COUNT = 5 };
+enum Choice { CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_SIMT = 3, CH_COUNT = 4 };
 
 struct GemmLaunch {
     CUtensorMap tmap;  // A of a TMA-mode tensor-core launch (64-byte aligned)
@@ -317,6 +325,14 @@ struct xeb_plan_s {
     // in node_mask[v] changed since the previous slice (all ones: always)
     std::vector<uint32_t> node_mask;
     int n_reused = 0;         // nodes whose result is kept across slices
+    // constant folding: subtrees that depend on no output bit, no sliced leg
+    // and no open leg are evaluated once on the host in FP64 (fold_roots: the
+    // largest such subtrees, their values in the root node's stored layout);
+    // their leaves and contractions never run on the device
+    std::vector<char> folded;          // per node: inside a folded subtree
+    std::vector<char> op_folded;       // per program op
+    std::vector<int> fold_roots;
+    std::vector<std::vector<cd>> fold_vals;
     Tree tree;
     std::vector<int> sliced;
     Analysis an;
@@ -337,7 +353,7 @@ struct xeb_plan_s {
     size_t bytes_total = 0;
     // offsets inside tables (bytes)
     int64_t t_trie_desc = 0, t_internal = 0, t_leaf_desc = 0, t_pi = 0, t_bits = 0, t_acc = 0, t_amps = 0,
-            t_partials = 0, t_result = 0, t_err = 0, t_wimg = 0, t_sort = 0, t_memo = 0;
+            t_partials = 0, t_result = 0, t_err = 0, t_sort = 0, t_memo = 0;
     size_t memo_bytes = 0;
     std::vector<int> choice;   // per op: CH_AUTO or the autotuner's form
     std::vector<int64_t> slice_ids;  // seeded subset of slice values (empty: all)
@@ -346,7 +362,8 @@ struct xeb_plan_s {
     std::vector<xebk::TrieDesc> trie;
     std::vector<int> trie_of_node;  // node -> index in trie, -1 if no bits
     std::vector<int> trie_internal;
-    std::vector<xebk::LeafDesc> leafdesc;
+    std::vector<xebk::LeafDesc> leafdesc;   // leaves materialised on the device
+    std::vector<int> leafdesc_leaf;         // ... their leaf ids
     std::vector<int64_t> leaf_src_off;
     int64_t leafdata_elems = 0;
     std::vector<xebk::PermDesc> perms;  // per op (unused for GEMM)
@@ -530,8 +547,7 @@ bool evaluate(const Network& net, const Tree& tree, const std::vector<int>& slic
     const Tree& tree_ = cand.tree;
     if (!analyze(net, tree_, sliced, cand.an, err)) return false;
     fill_counts(cand.an, dc);
-    build_program(cand.an, cand.prog, o.reserved[0] == 0,
-                  o.precision == XEB_PREC_TF32X3 && o.reserved[1] != 1);
+    build_program(cand.an, cand.prog, o.reserved[0] == 0, o.precision == XEB_PREC_TF32X3);
     plan_memory(cand.prog);
     cand.costs = tree_costs(cand.an, cand.prog, k);
     cand.arena_bytes = cand.prog.arena_elems * int64_t(elem);
@@ -736,6 +752,138 @@ void setup_reuse(xeb_plan_s* p) {
     p->n_reused = int(keep.size());
 }
 
+// Host FP64 tensor: legs slowest first, element index bit (size-1-i) = leg i.
+struct HostT {
+    std::vector<int> legs;
+    std::vector<cd> t;
+};
+
+// Pairwise contraction (Eq. elem-cont) of two host tensors over their shared
+// legs; result legs: a's unshared legs, then b's.
+HostT host_contract(const HostT& a, const HostT& b) {
+    std::vector<int> sh, fa, fb;
+    for (int l : a.legs)
+        (std::find(b.legs.begin(), b.legs.end(), l) != b.legs.end() ? sh : fa).push_back(l);
+    for (int l : b.legs)
+        if (std::find(sh.begin(), sh.end(), l) == sh.end()) fb.push_back(l);
+    auto bit_of = [](const std::vector<int>& lay, int leg) {
+        return int(lay.size()) - 1 - int(std::find(lay.begin(), lay.end(), leg) - lay.begin());
+    };
+    HostT r;
+    r.legs = fa;
+    r.legs.insert(r.legs.end(), fb.begin(), fb.end());
+    const int no = int(r.legs.size()), ns = int(sh.size());
+    std::vector<int64_t> oa(no, 0), ob(no, 0), sa(ns), sb(ns);
+    for (int i = 0; i < no; ++i) {
+        const int leg = r.legs[i];
+        const bool in_a = i < int(fa.size());
+        (in_a ? oa : ob)[no - 1 - i] = int64_t(1) << bit_of(in_a ? a.legs : b.legs, leg);
+    }
+    for (int j = 0; j < ns; ++j) {
+        sa[j] = int64_t(1) << bit_of(a.legs, sh[j]);
+        sb[j] = int64_t(1) << bit_of(b.legs, sh[j]);
+    }
+    r.t.assign(size_t(1) << no, cd(0, 0));
+    for (int64_t o = 0; o < (int64_t(1) << no); ++o) {
+        int64_t ia = 0, ib = 0;
+        for (int i = 0; i < no; ++i)
+            if ((o >> i) & 1) { ia += oa[i]; ib += ob[i]; }
+        cd acc(0, 0);
+        for (int64_t u = 0; u < (int64_t(1) << ns); ++u) {
+            int64_t ja = ia, jb = ib;
+            for (int j = 0; j < ns; ++j)
+                if ((u >> j) & 1) { ja += sa[j]; jb += sb[j]; }
+            acc += a.t[size_t(ja)] * b.t[size_t(jb)];
+        }
+        r.t[size_t(o)] = acc;
+    }
+    return r;
+}
+
+// Constant folding (see xeb_plan_s::folded).  A node qualifies when its
+// subtree depends on no output bit, sliced leg or open leg and every tensor in
+// it has at most max_legs legs; the qualifying internal nodes whose parent
+// does not qualify are evaluated on the host and their buffers reserved for
+// the whole step.  Off in permute-first mode.
+void fold_constants(xeb_plan_s* p) {
+    const Analysis& an = p->an;
+    const int N = int(an.nodes.size()), L = an.L;
+    p->folded.assign(size_t(N), 0);
+    p->op_folded.assign(p->prog.ops.size(), 0);
+    p->fold_roots.clear();
+    p->fold_vals.clear();
+    const int max_legs = p->opts.fold_legs == 0 ? 16 : p->opts.fold_legs;
+    if (max_legs < 0 || p->opts.reserved[0] == 1) return;
+    std::vector<char> ok(size_t(N), 0);
+    for (int v = 0; v < N; ++v) {
+        const Node& nd = an.nodes[size_t(v)];
+        bool q = nd.qmask == 0 && int(nd.legs.size()) <= max_legs && nd.q + int(nd.legs.size()) <= 24;
+        if (v < L) {
+            for (int l : p->net.leaves[size_t(v)].legs)
+                q = q && !p->net.is_open_leg(l) &&
+                    std::find(p->sliced.begin(), p->sliced.end(), l) == p->sliced.end();
+            q = q && p->net.leaves[size_t(v)].out_q.empty();
+        } else {
+            q = q && ok[size_t(nd.l)] && ok[size_t(nd.r)];
+        }
+        ok[size_t(v)] = q;
+    }
+    std::vector<HostT> val(static_cast<size_t>(N));
+    for (int v = L; v < N - 1; ++v) {
+        const Node& nd = an.nodes[size_t(v)];
+        if (!ok[size_t(v)] || ok[size_t(nd.parent)]) continue;
+        // evaluate the subtree of v in post-order (children have smaller ids)
+        std::vector<int> sub, stack{v};
+        while (!stack.empty()) {
+            const int u = stack.back();
+            stack.pop_back();
+            sub.push_back(u);
+            p->folded[size_t(u)] = 1;
+            if (u >= L) {
+                stack.push_back(an.nodes[size_t(u)].l);
+                stack.push_back(an.nodes[size_t(u)].r);
+            }
+        }
+        std::sort(sub.begin(), sub.end());
+        for (int u : sub) {
+            if (u < L) {
+                val[size_t(u)].legs = p->net.leaves[size_t(u)].legs;
+                val[size_t(u)].t = p->net.leaves[size_t(u)].t;
+            } else {
+                val[size_t(u)] = host_contract(val[size_t(an.nodes[size_t(u)].l)], val[size_t(an.nodes[size_t(u)].r)]);
+                val[size_t(an.nodes[size_t(u)].l)] = HostT();
+                val[size_t(an.nodes[size_t(u)].r)] = HostT();
+            }
+        }
+        // values in the stored layout of v's result
+        const HostT& h = val[size_t(v)];
+        const std::vector<int>& lay = p->prog.layout[size_t(v)];
+        const int r = int(lay.size());
+        std::vector<int64_t> inc(static_cast<size_t>(r));
+        for (int i = 0; i < r; ++i) {
+            const int at = int(std::find(h.legs.begin(), h.legs.end(), lay[size_t(i)]) - h.legs.begin());
+            inc[size_t(r - 1 - i)] = int64_t(1) << (int(h.legs.size()) - 1 - at);
+        }
+        std::vector<cd> out(size_t(1) << r);
+        for (int64_t x = 0; x < (int64_t(1) << r); ++x) {
+            int64_t src = 0;
+            for (int i = 0; i < r; ++i)
+                if ((x >> i) & 1) src += inc[size_t(i)];
+            out[size_t(x)] = h.t[size_t(src)];
+        }
+        val[size_t(v)] = HostT();
+        p->fold_roots.push_back(v);
+        p->fold_vals.push_back(std::move(out));
+        Buffer& b = p->prog.bufs[size_t(p->prog.node_buf[size_t(v)])];
+        b.first = 0;
+        b.last = int(p->prog.ops.size()) + 1;
+    }
+    if (p->fold_roots.empty()) return;
+    for (size_t i = 0; i < p->prog.ops.size(); ++i)
+        p->op_folded[i] = p->prog.ops[i].kind == OP_GEMM && p->folded[size_t(p->prog.ops[i].node)];
+    plan_memory(p->prog);
+}
+
 xeb_status create_plan(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k, uint64_t open_mask,
                        const xeb_tree* tree, const xeb_slices* slices, const xeb_plan_opts* opts, xeb_plan_s** out) {
     if (!out) return fail(XEB_EINVAL, "out is NULL");
@@ -749,6 +897,11 @@ xeb_status create_plan(const xeb_circuit* circuit, const uint64_t* bitstrings, s
     const xeb_plan_opts& o = p->opts;
     if (o.precision != XEB_PREC_FP32 && o.precision != XEB_PREC_FP64 && o.precision != XEB_PREC_TF32X3)
         return fail(XEB_EINVAL, "unknown precision");
+    if (o.split_bits != 0 && (o.split_bits < 8 || o.split_bits > 11))
+        return fail(XEB_EINVAL, "split_bits must be 0 (default) or 8..11");
+    if (o.split_terms != 0 && o.split_terms != 3 && o.split_terms != 4)
+        return fail(XEB_EINVAL, "split_terms must be 0 (default), 3 or 4");
+    if (o.timeout_ms > 600000) return fail(XEB_EINVAL, "timeout_ms above 600000 (ten minutes)");
     p->elem = o.precision == XEB_PREC_FP64 ? 16 : 8;
     std::string err;
     if (!build_network(circuit, p->net, err, open_mask)) return fail(XEB_EINVAL, err);
@@ -856,6 +1009,7 @@ xeb_status create_plan(const xeb_circuit* circuit, const uint64_t* bitstrings, s
             p->rootmap.pos[j] = int8_t(int(lay.size()) - 1 - at);
         }
     }
+    fold_constants(p.get());
     setup_reuse(p.get());
     *out = p.release();
     return XEB_OK;
@@ -957,9 +1111,11 @@ extern "C" xeb_status xeb_plan_stats(xeb_plan_s* p, xeb_stats* s) {
     }
     s->planner_used = p->planner_used;
     s->reserved[0] = p->n_reused;
+    for (char f : p->folded) s->reserved[1] += f != 0;
+    s->reserved[2] = int(p->fold_roots.size());
     for (size_t i = 0; i < p->gemms.size() && i < p->prog.ops.size(); ++i)
         if (const GemmLaunch& g = p->gemms[i];
-            p->prog.ops[i].kind != OP_PERM && (g.kernel == GK_TC || g.kernel == GK_TC2)) {
+            p->prog.ops[i].kind != OP_PERM && !p->op_folded[i] && g.kernel == GK_TC2) {
             ++s->n_tc_launches;
             s->n_tc_tma += g.tc.tma != 0;
         }
@@ -1070,7 +1226,6 @@ void layout_device(xeb_plan_s* p) {
     p->t_partials = take(int64_t(p->n_xeb_blocks) * 16);
     p->t_result = take(64);
     p->t_err = take(16);
-    p->t_wimg = take(p->opts.precision == XEB_PREC_TF32X3 ? 2 * 4 * 128 * 32 * 4 : 16);
     p->t_sort = take(p->k > size_t(xebk::kMaxTrieK) ? int64_t(xebk::trie_sort_scratch_bytes(int(p->k))) : 16);
     {   // memo-level contractions: per-group A offsets + packed B vectors (largest op)
         size_t mx = 16;
@@ -1085,22 +1240,79 @@ void layout_device(xeb_plan_s* p) {
     p->bytes_total = size_t(off + t);
 }
 
+}  // namespace
+
+// Norm-keeping rounding of a leaf to single precision (see xeb.h,
+// xeb_round_keep_norm): nearest values first, then, cheapest first, values
+// move to their other neighbour while that brings sum y^2 closer to sum x^2.
+extern "C" void xeb_round_keep_norm(const double* x, size_t n, float* y) {
+    if (!x || !y) return;
+    long double err = 0;
+    std::vector<std::pair<double, size_t>> cand;
+    std::vector<float> other(n);
+    for (size_t i = 0; i < n; ++i) {
+        const float r = float(x[i]);
+        y[i] = r;
+        err += (long double)r * r - (long double)x[i] * x[i];
+        if (double(r) == x[i] || !std::isfinite(r)) continue;
+        other[i] = std::nextafter(r, double(r) > x[i] ? -INFINITY : INFINITY);
+        cand.push_back({std::fabs(double(other[i]) - x[i]) - std::fabs(double(r) - x[i]), i});
+    }
+    std::sort(cand.begin(), cand.end());
+    for (const auto& c : cand) {
+        const size_t i = c.second;
+        const long double d = (long double)other[i] * other[i] - (long double)y[i] * y[i];
+        if (std::fabs(double(err + d)) < std::fabs(double(err))) {
+            err += d;
+            y[i] = other[i];
+        }
+    }
+}
+
+namespace {
+
+// Device values of one constant tensor (a leaf or a folded subtree): complex64
+// plans round with xeb_round_keep_norm (opts.reserved[1] = 0 or 2) or to
+// nearest (1); an FP64 plan keeps the exact values (0) or takes those
+// single-precision values (1, 2: the error the rounding alone causes).
+void constant_to_device(const xeb_plan_s* p, const std::vector<cd>& t, char* dst) {
+    const int mode = p->opts.reserved[1];
+    std::vector<double> x(2 * t.size());
+    std::vector<float> y(x.size());
+    for (size_t e = 0; e < t.size(); ++e) {
+        x[2 * e] = t[e].real();
+        x[2 * e + 1] = t[e].imag();
+    }
+    const bool single = p->elem == 8 || mode != 0;
+    if (single && mode == 1) {
+        for (size_t i = 0; i < x.size(); ++i) y[i] = float(x[i]);
+    } else if (single) {
+        xeb_round_keep_norm(x.data(), x.size(), y.data());
+    }
+    if (p->elem == 8) {
+        std::memcpy(dst, y.data(), y.size() * sizeof(float));
+    } else {
+        double* d = reinterpret_cast<double*>(dst);
+        for (size_t i = 0; i < x.size(); ++i) d[i] = single ? double(y[i]) : x[i];
+    }
+}
+
 std::vector<char> leaf_host_data(xeb_plan_s* p) {
     std::vector<char> h(size_t(p->leafdata_elems) * p->elem);
-    for (size_t j = 0; j < p->net.leaves.size(); ++j) {
-        const Leaf& lf = p->net.leaves[j];
-        for (size_t e = 0; e < lf.t.size(); ++e) {
-            const int64_t idx = p->leaf_src_off[j] + int64_t(e);
-            if (p->elem == 8) {
-                float* f = reinterpret_cast<float*>(h.data()) + 2 * idx;
-                f[0] = float(lf.t[e].real());
-                f[1] = float(lf.t[e].imag());
-            } else {
-                double* d = reinterpret_cast<double*>(h.data()) + 2 * idx;
-                d[0] = lf.t[e].real();
-                d[1] = lf.t[e].imag();
-            }
-        }
+    for (size_t j = 0; j < p->net.leaves.size(); ++j)
+        constant_to_device(p, p->net.leaves[j].t, h.data() + size_t(p->leaf_src_off[j]) * p->elem);
+    return h;
+}
+
+// the folded constants, one after another in fold_roots order
+std::vector<char> fold_host_data(xeb_plan_s* p) {
+    size_t n = 0;
+    for (const auto& v : p->fold_vals) n += v.size();
+    std::vector<char> h(n * p->elem);
+    size_t at = 0;
+    for (const auto& v : p->fold_vals) {
+        constant_to_device(p, v, h.data() + at);
+        at += v.size() * p->elem;
     }
     return h;
 }
@@ -1115,18 +1327,19 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
         g.tc.a_off = d.a_off;
         g.tc.b_off = grouped ? 0 : d.b_off;
         g.tc.c_off = d.c_off;
-        g.tc.wimg = reinterpret_cast<float*>(tables + p->t_wimg);
         g.tc.err = reinterpret_cast<int32_t*>(tables + p->t_err);
+        g.tc.split_bits = p->opts.split_bits > 0 ? p->opts.split_bits : kSplitBitsDefault;
+        g.tc.split_terms = p->opts.split_terms > 0 ? p->opts.split_terms : kSplitTermsDefault;
+        g.tc.wait_ns = uint64_t(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : kTimeoutMsDefault) * 1000000ull;
         std::memset(&g.tmap, 0, sizeof(g.tmap));
     };
     if (op.M == 1 && op.N == 1) {
         g.kernel = xebk::GK_TAIL;
         return ch == CH_AUTO || ch == CH_SIMT;
     }
-    const bool smem_w = ch == CH_TC1 || (ch == CH_AUTO && p->opts.reserved[1] == 1);
-    const bool tc_ok = tf32 && (ch == CH_AUTO || ch == CH_TC2 || ch == CH_TC2_GATHER || ch == CH_TC1);
-    if (tc_ok && tc_tile(op, g.tc, smem_w ? 7 : xebk::kTc2RowBits, !smem_w)) {
-        g.kernel = smem_w ? GK_TC : GK_TC2;
+    const bool tc_ok = tf32 && (ch == CH_AUTO || ch == CH_TC2 || ch == CH_TC2_GATHER);
+    if (tc_ok && tc_tile(op, g.tc, xebk::kTc2RowBits, true)) {
+        g.kernel = GK_TC2;
         tc_common(false);
         const bool gather = ch == CH_TC2_GATHER || (ch == CH_AUTO && p->opts.reserved[3] == 1);
         if (g.tc.tma && (gather || !encode_a_map(g.tc, reinterpret_cast<const float2*>(p->ws + p->off_arena), g.tmap)))
@@ -1136,14 +1349,14 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
     // keyed tensor-core form: an autotuner choice, or the default with
     // opts.reserved[6] = 1 (on the 53-qubit plans, whose keyed contractions
     // are mostly K = N = 16, it ran no faster than the SIMT kernels)
-    if (tc_ok && !smem_w && (ch == CH_TC2_GATHER || (ch == CH_AUTO && p->opts.reserved[6] == 1)) &&
+    if (tc_ok && (ch == CH_TC2_GATHER || (ch == CH_AUTO && p->opts.reserved[6] == 1)) &&
         tc_keyed(op, d, g.tc)) {
         g.kernel = GK_TC2;
         tc_common(false);
         return true;
     }
     if (tc_ok && ch != CH_AUTO) return false;
-    if (tf32 && (ch == CH_GROUPED || (ch == CH_AUTO && p->opts.reserved[1] != 1 && p->opts.reserved[4] == 1)) &&
+    if (tf32 && (ch == CH_GROUPED || (ch == CH_AUTO && p->opts.reserved[4] == 1)) &&
         tc_grouped(p->an, op, d, g.tc)) {
         g.kernel = GK_TC2;
         tc_common(true);
@@ -1170,11 +1383,15 @@ void build_launches(xeb_plan_s* p) {
     const Program& pr = p->prog;
     const int L = an.L;
     char* tables = p->ws + p->off_tables;
-    // leaves
-    p->leafdesc.assign(L, xebk::LeafDesc{});
+    // leaves (those inside folded subtrees are never materialised)
+    p->leafdesc.clear();
+    p->leafdesc_leaf.clear();
     for (int j = 0; j < L; ++j) {
+        if (!p->folded.empty() && p->folded[size_t(j)]) continue;
         const Leaf& lf = p->net.leaves[j];
-        xebk::LeafDesc& d = p->leafdesc[j];
+        p->leafdesc_leaf.push_back(j);
+        p->leafdesc.push_back(xebk::LeafDesc{});
+        xebk::LeafDesc& d = p->leafdesc.back();
         d.dst_off = pr.bufs[pr.node_buf[j]].off;
         d.src_off = p->leaf_src_off[j];
         const std::vector<int>& lay = pr.layout[j];
@@ -1345,11 +1562,11 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 return false;
             }
         }
-        if (p->gemms[i].kernel == GK_TC || p->gemms[i].kernel == GK_TC2) {
+        if (p->gemms[i].kernel == GK_TC2) {
             const xebk::TcDesc& t = p->gemms[i].tc;
-            const int row_bits = p->gemms[i].kernel == GK_TC2 ? xebk::kTc2RowBits : 7;
+            const int row_bits = xebk::kTc2RowBits;
             // grouped memo-level form: the columns are a group's keys (N2/2 of them at most)
-            const bool grp = p->gemms[i].kernel == GK_TC2 && t.grp;
+            const bool grp = t.grp;
             const bool keyed = grp && t.keyed;   // keyed form: the op's own K x N per key
             const bool mgrp = grp && !t.keyed;   // memo-level groups: keys as columns
             int lnp = 0;
@@ -1358,8 +1575,8 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
             const int nbn_eff = mgrp ? lnp : g.nbn;
             if (t.M != g.M || t.M % (int64_t(1) << row_bits) != 0 || t.K2 != 2 * g.K || t.N2 != 2 * gN ||
                 t.K2 % 32 != 0 || t.N2 % 32 != 0 || t.N2 > 128 || t.K2 > 128 || t.n_chunks * 32 != t.K2 ||
-                t.n_chunks > 4 || t.T != row_bits + 4 || (!grp && g.kv != 1) ||
-                xebk::tc_wimg_floats(t) * 4 > size_t(2 * 4 * 128 * 32 * 4)) {
+                t.n_chunks > 4 || t.T != row_bits + 4 || (!grp && g.kv != 1) || t.split_bits < 8 ||
+                t.split_bits > 11 || (t.split_terms != 3 && t.split_terms != 4) || t.wait_ns == 0) {
                 why = "tensor-core tile of node " + std::to_string(op.node);
                 return false;
             }
@@ -1375,20 +1592,13 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 why = "grouped tensor-core form of node " + std::to_string(op.node);
                 return false;
             }
-            // largest element a loader can touch
-            int64_t hi = 0;
-            for (int i = 0; i < t.T; ++i) hi |= int64_t(1) << t.pos[i];
-            hi += t.chunk_off[t.n_chunks - 1];
-            int64_t rowhi = 0;
-            for (int i = row_bits; i < t.nam; ++i) rowhi |= int64_t(1) << t.apm[i];
-            if ((p->gemms[i].kernel == GK_TC && !inside(op.a_buf, t.a_off, t.a_off + rowhi + hi)) ||
-                (!grp && !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1))) {
+            if (!grp && !inside(op.c_buf, t.c_off, t.c_off + g.M * g.N - 1)) {
                 why = "tensor-core operand of node " + std::to_string(op.node);
                 return false;
             }
             for (int i = 0; i < t.T; ++i)
                 if (t.pos[i] < 0 || t.pos[i] >= op.a_rank) { why = "tensor-core tile positions"; return false; }
-            if (p->gemms[i].kernel == GK_TC2) {
+            {
                 const int rc = g.nam + nbn_eff;
                 if (t.n_ext + row_bits != g.nam || t.n_ext > 32 || t.Tst != row_bits + nbn_eff || t.Tst < row_bits + 4 ||
                     t.Tst > 16) {
@@ -1444,7 +1654,7 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
     }
     for (size_t j = 0; j < p->leafdesc.size(); ++j) {
         const xebk::LeafDesc& d = p->leafdesc[j];
-        if (!inside(pr.node_buf[j], d.dst_off, d.dst_off + (int64_t(d.kv) << d.r) - 1)) { why = "leaf dst"; return false; }
+        if (!inside(pr.node_buf[size_t(p->leafdesc_leaf[j])], d.dst_off, d.dst_off + (int64_t(d.kv) << d.r) - 1)) { why = "leaf dst"; return false; }
         if (d.src_off + (int64_t(1) << d.n_canon) > p->leafdata_elems) { why = "leaf src"; return false; }
         for (int b = 0; b < d.r; ++b)
             if (d.src_pos[b] < 0 || d.src_pos[b] >= d.n_canon - d.n_out) { why = "leaf layout"; return false; }
@@ -1456,9 +1666,7 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
 template <typename T>
 cudaError_t launch_gemm_op(xeb_plan_s* p, const GemmLaunch& g, T* arena, char* tables, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
-    if (g.kernel == GK_TC) {
-        if constexpr (sizeof(T) == 8) e = xebk::launch_tc_gemm(g.tc, reinterpret_cast<float2*>(arena), p->n_sms, st);
-    } else if (g.kernel == GK_TC2) {
+    if (g.kernel == GK_TC2) {
         if constexpr (sizeof(T) == 8) {
             if (g.tc.grp) e = xebk::launch_memo_prep<float2>(g.d, reinterpret_cast<float2*>(arena), tables + p->t_memo, st);
             if (e == cudaSuccess) e = xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st);
@@ -1493,7 +1701,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
         s_prev = s;
         {
             ProfScope ps(p, st, XEB_KC_LEAVES, 0.0, 0.0);
-            XEB_CUDA(xebk::launch_leaves<T>(ldesc, an.L, leafdata, arena, tables, s, st));
+            XEB_CUDA(xebk::launch_leaves<T>(ldesc, int(p->leafdesc.size()), leafdata, arena, tables, s, st));
         }
         for (size_t i = 0; i < pr.ops.size(); ++i) {
             const Op& op = pr.ops[i];
@@ -1502,6 +1710,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 XEB_CUDA(xebk::launch_permute<T>(p->perms[i], arena + pr.bufs[op.src_buf].off,
                                                  arena + pr.bufs[op.dst_buf].off, st));
             } else {
+                if (p->op_folded[i]) continue;   // evaluated on the host at plan creation
                 if (si > 0 && !(changed & p->node_mask[size_t(op.node)])) continue;   // still holds this slice's value
                 const GemmLaunch& g = p->gemms[i];
                 const double ka = double(an.nodes[op.a_node].kv), kb = double(an.nodes[op.b_node].kv);
@@ -1511,7 +1720,7 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 static const int cls_of[7] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
                                               XEB_KC_GEMM_TAIL,    XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO,
                                               XEB_KC_GEMM_KDEEP};
-                ProfScope ps(p, st, g.kernel >= GK_TC ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by, int(i));
+                ProfScope ps(p, st, g.kernel >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by, int(i));
                 XEB_CUDA(launch_gemm_op<T>(p, g, arena, tables, st));
             }
         }
@@ -1612,6 +1821,15 @@ extern "C" xeb_status xeb_plan_bind(xeb_plan_s* p, void* workspace, size_t bytes
     const std::vector<char> leafdata = leaf_host_data(p);
     std::vector<int32_t> pi(p->an.pi.begin(), p->an.pi.end());
     XEB_CUDA(cudaMemcpyAsync(p->ws + p->off_leafdata, leafdata.data(), leafdata.size(), cudaMemcpyHostToDevice, st));
+    // folded constants: into their (reserved) arena buffers, once
+    const std::vector<char> foldbytes = fold_host_data(p);
+    for (size_t f = 0, at = 0; f < p->fold_roots.size(); ++f) {
+        const size_t n = p->fold_vals[f].size() * p->elem;
+        const int64_t off = p->prog.bufs[size_t(p->prog.node_buf[size_t(p->fold_roots[f])])].off;
+        XEB_CUDA(cudaMemcpyAsync(p->ws + p->off_arena + off * int64_t(p->elem), foldbytes.data() + at, n,
+                                 cudaMemcpyHostToDevice, st));
+        at += n;
+    }
     XEB_CUDA(cudaMemcpyAsync(tables + p->t_trie_desc, p->trie.data(), p->trie.size() * sizeof(xebk::TrieDesc),
                              cudaMemcpyHostToDevice, st));
     XEB_CUDA(cudaMemcpyAsync(tables + p->t_internal, p->trie_internal.data(), p->trie_internal.size() * 4,
@@ -1944,7 +2162,7 @@ extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t strea
     int changed = 0;
     std::string why;
     for (size_t i = 0; i < pr.ops.size() && s == XEB_OK; ++i) {
-        if (pr.ops[i].kind == OP_PERM) continue;
+        if (pr.ops[i].kind == OP_PERM || p->op_folded[i]) continue;
         const GemmLaunch keep = p->gemms[i];
         std::vector<std::pair<float, int>> timed;
         std::vector<std::pair<int, int>> seen;
@@ -2018,8 +2236,9 @@ extern "C" xeb_status xeb_plan_step_flops(const xeb_plan_s* p, double* flops, do
     const int S = int(p->sliced.size());
     const int64_t n_run = p->slice_ids.empty() ? int64_t(1) << S : int64_t(p->slice_ids.size());
     double fl = 0, nc = 0;
-    for (const Op& op : p->prog.ops) {
-        if (op.kind != OP_GEMM) continue;
+    for (size_t i = 0; i < p->prog.ops.size(); ++i) {
+        const Op& op = p->prog.ops[i];
+        if (op.kind != OP_GEMM || p->op_folded[i]) continue;
         const uint32_t e = p->node_mask[size_t(op.node)];
         double times = 0;
         if (p->slice_ids.empty()) {   // counting order: bit b moves every 2^b slices
@@ -2074,7 +2293,7 @@ extern "C" xeb_status xeb_plan_profile_ops(xeb_plan_s* p, int cap, double* ms, d
             else if (!p->bound || p->gemms.size() <= size_t(i)) cls[i] = -1;
             else {
                 const int kk = p->gemms[size_t(i)].kernel;
-                cls[i] = kk >= GK_TC ? XEB_KC_GEMM_TC : cls_of[kk];
+                cls[i] = kk >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[kk];
             }
         }
         if (shape) {

@@ -387,6 +387,7 @@ __global__ void k_leaves(const LeafDesc* desc, const T* leafdata, T* arena, cons
 template <typename T>
 cudaError_t launch_leaves(const LeafDesc* d_desc, int n_leaves, const T* leafdata, T* arena,
                           const char* tables, int64_t slice, cudaStream_t st) {
+    if (n_leaves <= 0) return cudaSuccess;
     k_leaves<T><<<n_leaves, 128, 0, st>>>(d_desc, leafdata, arena, tables, slice);
     return cudaGetLastError();
 }

@@ -115,8 +115,12 @@ struct TcDesc {
     // x is the XOR of st_swz[i] over the tile bits i (ascending C address
     // order) set in (row, n); st_swz[i] < 16 and is 0 for column bits below 4
     int8_t st_swz[16];
-    float* wimg;          // scratch: split, swizzled image of the real-expanded B
     int32_t* err;         // error word (timeouts)
+    // split of the operands (see tc_gemm2.cu): big parts on a common grid of
+    // 2^split_bits units per state row and chunk / per W^T row; split_terms =
+    // 3 (big*big, big*small, small*big) or 4 (+ small*small)
+    int split_bits, split_terms;
+    uint64_t wait_ns;     // limit of every device-side wait (ns of %globaltimer)
     // (tensor-memory variant, TMA mode) A is a row-major [M][K] matrix; a
     // chunk is 2^(kTc2RowBits - box_log2) boxes of 32 floats x 2^box_log2
     // consecutive rows; box j starts box_y[j] rows above the tile's base row,
@@ -143,7 +147,6 @@ struct TcDesc {
 };
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 constexpr int kTc2RowBits = 7;               // tensor-memory variant: 128 state rows per tile
-size_t tc_wimg_floats(const TcDesc& t);
 
 // ---- launch wrappers (all asynchronous on `st`) --------------------------------
 // Raise the dynamic shared-memory limits of every kernel (once per process,
@@ -179,10 +182,9 @@ template <typename T>
 cudaError_t launch_memo_prep(const GemmDesc& g, T* arena, char* scratch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_root_accum(const T* root, double2* acc, int64_t kv, cudaStream_t st);
-cudaError_t launch_tc_gemm(const TcDesc& t, float2* arena, int n_sms, cudaStream_t st);
-// Variant with W^T in tensor memory and a deep cp.async ring (64-row tiles,
-// tile bits = 6 row bits + 4 k bits).
-// tmap: 2-D tensor map of A (used when t.tma != 0)
+// tcgen05 split-precision contraction with W^T in tensor memory (128-row
+// tiles, tile bits = 7 row bits + 4 k bits); tmap: 2-D tensor map of A (used
+// when t.tma != 0)
 cudaError_t launch_tc_gemm2(const TcDesc& t, const CUtensorMap& tmap, float2* arena, int n_sms, cudaStream_t st);
 // Multi-batch plans: the root tensor of each key holds 2^w values, one per
 // value x of the open qubits; bit j of x (open qubits in ascending order)

@@ -1,12 +1,27 @@
 // Split-precision complex contraction on tcgen05 with the small operand in
 // tensor memory.
 //
-// Same arithmetic as tc_gemm.cu (C' = A' W with the real expansion
-// W = [[Re B, Im B], [-Im B, Re B]] interleaved, operands split into RN-TF32
-// big + small, three products, big*big and the cross terms in separate FP32
-// accumulators), with the roles of the MMA operands swapped:
+// The complex product C = A B is computed as the real product C' = A' W with
+// W = [[Re B, Im B], [-Im B, Re B]] interleaved, in the operand roles
 //
 //     D (2N x rows) = W^T (2N x 2K) * A'^T (2K x rows)
+//
+// Split precision: every FP32 operand value x is split into x = big + small
+// with small = RN_tf32(x - big), and D = big*big + big*small + small*big (+
+// small*small with split_terms = 4).  big*big goes into its own FP32
+// accumulator, the cross terms into another; the two are added with
+// round-to-nearest in the epilogue.  The tensor cores truncate when they
+// accumulate, which biases a long sum of products toward zero; over a chain of
+// contractions that bias would shift every probability, and with it F, by
+// many times the amplitude error.  So the big parts are not rounded per value:
+// the bigs of one group -- one state row of one 32-float K-chunk, one row of
+// W^T over all of K -- are the group's values rounded to the nearest multiple
+// of the unit u = 2^(e - split_bits + 1), 2^e <= (largest |x| of the group) <
+// 2^(e+1).  Each big is then an integer of at most split_bits bits times u
+// (an exact TF32 value), every big*big product of one output element is an
+// integer multiple of u_row * u_col, and their sum is exact in FP32 as long as
+// it stays below 2^24 such units: no truncation happens.  The small parts
+// carry the rest of each value to 11 more bits.
 //
 // W^T (big and small, <= 128 x 128 floats each) is written once per CTA into
 // tensor memory and serves as the MMA's A operand; the state rows are the
@@ -59,7 +74,6 @@ template <bool kTma>
 __host__ __device__ constexpr int op_stages() { return kTma ? kRingTma : kRingGather; }
 template <bool kTma>
 constexpr size_t ring_bytes() { return (kTma ? size_t(kRaw) * kRawBytes : 0) + size_t(op_stages<kTma>()) * kStageBytes; }
-constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -81,14 +95,16 @@ __device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t par) {
                  : "memory");
     return ok != 0;
 }
-__device__ bool bar_wait(uint64_t* b, uint32_t par, int32_t* err, int code) {
+// bounded wait: gives up (false) when the error word is set or after lim ns,
+// recording kErrTimeout | code
+__device__ bool bar_wait(uint64_t* b, uint32_t par, int32_t* err, int code, uint64_t lim) {
     if (bar_try(b, par)) return true;
     const uint64_t t0 = gtimer();
     for (uint32_t i = 0;; ++i) {
         if (bar_try(b, par)) return true;
         if ((i & 255) == 255) {
             if (*reinterpret_cast<volatile int32_t*>(err) != 0) return false;
-            if (gtimer() - t0 > kWaitNs) {
+            if (gtimer() - t0 > lim) {
                 atomicCAS(err, 0, kErrTimeout | code);
                 return false;
             }
@@ -96,11 +112,11 @@ __device__ bool bar_wait(uint64_t* b, uint32_t par, int32_t* err, int code) {
     }
 }
 // bounded wait that ignores the error word (waiting for copies in flight)
-__device__ void bar_wait_drain(uint64_t* b, uint32_t par) {
+__device__ void bar_wait_drain(uint64_t* b, uint32_t par, uint64_t lim) {
     const uint64_t t0 = gtimer();
     for (uint32_t i = 0;; ++i) {
         if (bar_try(b, par)) return;
-        if ((i & 255) == 255 && gtimer() - t0 > kWaitNs) return;
+        if ((i & 255) == 255 && gtimer() - t0 > lim) return;
     }
 }
 __device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
@@ -120,8 +136,33 @@ __device__ __forceinline__ float tf32_rn(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
-__device__ __forceinline__ float4 tf32_rn4(float4 v) {
-    return make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+// Common-grid split (see the top of the file).  grid_c(m, bits) is the
+// constant c = 1.5 * 2^(e - bits + 24) for a group whose largest magnitude m
+// lies in [2^e, 2^(e+1)): for |x| <= m, (x + c) - c rounds x to the nearest
+// multiple of u = 2^(e - bits + 1) (ties to even), because x + c stays in the
+// binade of c whose spacing is u; the subtraction is exact.  m = 0 or a
+// subnormal m takes e = -126.
+__device__ __forceinline__ float grid_c(float m, int bits) {
+    int ex = int((__float_as_uint(m) >> 23) & 0xffu);   // biased exponent of m (m >= 0)
+    ex = ex < 1 ? 1 : ex;
+    int cex = ex + 24 - bits;                            // biased exponent of c
+    cex = cex > 254 ? 254 : cex;
+    return __uint_as_float((uint32_t(cex) << 23) | 0x400000u);
+}
+__device__ __forceinline__ float grid_big(float x, float c) { return __fsub_rn(__fadd_rn(x, c), c); }
+// big and small parts of x on the grid of c
+__device__ __forceinline__ void split_on(float x, float c, float& big, float& small) {
+    big = grid_big(x, c);
+    small = tf32_rn(__fsub_rn(x, big));
+}
+__device__ __forceinline__ float absmax4(float4 v) {
+    return fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+}
+__device__ __forceinline__ void split4(float4 v, float c, float4& b, float4& s) {
+    split_on(v.x, c, b.x, s.x);
+    split_on(v.y, c, b.y, s.y);
+    split_on(v.z, c, b.z, s.z);
+    split_on(v.w, c, b.w, s.w);
 }
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
@@ -174,7 +215,9 @@ __device__ __forceinline__ void tm_st32(uint32_t ta, const float* v) {
         : "memory");
 }
 struct Sm2 {
-    uint64_t full[kRingGather], empty[kRingGather], rfull[kRaw], rempty[kRaw], tfull[2], tempty[2], wready, drain, epi;
+    // rawb: gather mode, all producers have stored their raw values of a stage
+    uint64_t full[kRingGather], empty[kRingGather], rawb[kRingGather], rfull[kRaw], rempty[kRaw], tfull[2], tempty[2],
+        wready, drain, epi;
     uint32_t tmem, pad;
     // staging offset (floats) of tile row r = rlo[r % 32] ^ rhi[r / 32]: the
     // row's base r * kCStride with its column swizzle folded in (linear in r)
@@ -215,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < kRing; ++s) {
             bar_init(&S->full[s], kProdT);
             bar_init(&S->empty[s], 1);
+            bar_init(&S->rawb[s], kProdT);
         }
         for (int s = 0; s < kRaw; ++s) {
             bar_init(&S->rfull[s], 1);
@@ -255,24 +299,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (kTma && warp < kProdWarps) {
         // ---------------- TMA mode: split landed raw chunks into the operand ring ----------------
         // raw and operand stages are 1024-byte aligned, so the 128-byte swizzle
-        // the TMA applied is the layout the MMA reads: the split is a linear copy
+        // the TMA applied is the layout the MMA reads: the split is a linear
+        // copy.  A 128-byte line is one state row's 32 values of the chunk;
+        // thread tid splits line tid (its maximum is the row's grid), visiting
+        // the line's 16-byte units from (tid & 7) on, so the 8 lanes of each
+        // shared-memory phase touch 8 different bank groups.  The grid is
+        // found as soon as the chunk lands, before waiting for a free operand
+        // stage.
+        static_assert(!kTma || kProdT == kRows, "one split thread per tile row");
         const int64_t total = my_tiles * nch;
         for (int64_t c = 0; c < total; ++c) {
             const int s1 = int(c % kRaw), s2 = int(c % kRing);
-            if (!bar_wait(&S->rfull[s1], uint32_t(c / kRaw) & 1, t.err, 20)) break;
-            if (!bar_wait(&S->empty[s2], (uint32_t(c / kRing) & 1) ^ 1, t.err, 11)) break;
-            const float4* src = reinterpret_cast<const float4*>(rawr + s1 * kRawBytes);
-            float4* db = reinterpret_cast<float4*>(ring + s2 * kStageBytes);
-            float4* ds = db + kRawBytes / 16;
-            constexpr int kV = kRawBytes / 16 / kProdT;  // float4 per thread
-            float4 v[kV];
+            if (!bar_wait(&S->rfull[s1], uint32_t(c / kRaw) & 1, t.err, 20, t.wait_ns)) break;
+            const unsigned char* src = rawr + s1 * kRawBytes + tid * 128;
+            float4 v[8];
+            float m = 0.f;
 #pragma unroll
-            for (int i = 0; i < kV; ++i) v[i] = src[tid + kProdT * i];
+            for (int i = 0; i < 8; ++i) {
+                v[i] = *reinterpret_cast<const float4*>(src + 16 * ((i + tid) & 7));
+                m = fmaxf(m, absmax4(v[i]));
+            }
+            const float cg = grid_c(m, t.split_bits);
+            if (!bar_wait(&S->empty[s2], (uint32_t(c / kRing) & 1) ^ 1, t.err, 11, t.wait_ns)) break;
+            unsigned char* db = ring + s2 * kStageBytes + tid * 128;
+            unsigned char* ds = db + kRawBytes;
 #pragma unroll
-            for (int i = 0; i < kV; ++i) {
-                const float4 b = tf32_rn4(v[i]);
-                db[tid + kProdT * i] = b;
-                ds[tid + kProdT * i] = tf32_rn4(make_float4(v[i].x - b.x, v[i].y - b.y, v[i].z - b.z, v[i].w - b.w));
+            for (int i = 0; i < 8; ++i) {
+                float4 b, sm4;
+                split4(v[i], cg, b, sm4);
+                *reinterpret_cast<float4*>(db + 16 * ((i + tid) & 7)) = b;
+                *reinterpret_cast<float4*>(ds + 16 * ((i + tid) & 7)) = sm4;
             }
             bar_arrive(&S->rempty[s1]);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -296,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int64_t y0 = ybase(tile);
             for (; c < total; ++c) {
                 const int s = int(c % kRaw);
-                if (!bar_wait(&S->rempty[s], (uint32_t(c / kRaw) & 1) ^ 1, t.err, 18)) break;
+                if (!bar_wait(&S->rempty[s], (uint32_t(c / kRaw) & 1) ^ 1, t.err, 18, t.wait_ns)) break;
                 bar_expect_tx(&S->rfull[s], kRawBytes);
                 unsigned char* dst = rawr + s * kRawBytes;
                 for (int j = 0; j < nbox; ++j)
@@ -309,14 +365,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // the CTA must not exit with copies in flight: wait (bounded) for the last ones
             for (int64_t d = c > kRaw ? c - kRaw : 0; d < c; ++d)
-                bar_wait_drain(&S->rfull[d % kRaw], uint32_t(d / kRaw) & 1);
+                bar_wait_drain(&S->rfull[d % kRaw], uint32_t(d / kRaw) & 1, t.wait_ns);
         }
         __syncwarp();
     } else if (!kTma && warp < kProdWarps) {
         // ---------------- producers: gather into registers, split into the ring ----------------
-        // Each thread keeps the loads of kLook chunks in flight in registers;
-        // chunk c is split into big/small straight into its ring stage once
-        // the stage is free, then the loads of chunk c + kLook are issued.
+        // Each thread keeps the loads of kLook chunks in flight in registers.
+        // Chunk c is stored raw into the big half of its ring stage once the
+        // stage is free, then the loads of chunk c + kLook are issued.  When
+        // all producers have stored theirs (rawb), thread tid splits half
+        // (tid & 1) of tile row tid >> 1 in place: the row's grid needs all of
+        // its 32 values, which other threads loaded.
         int32_t off[kPerThread];
         uint32_t pos[kPerThread];
 #pragma unroll
@@ -369,6 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int u = 0; u < kLook; ++u)
             if (u < total) XEB_TC2_ISSUE(u);
+        static_assert(kTma || kProdT == 2 * kRows, "two producer threads per tile row in the split phase");
+        const int prow = tid >> 1, phalf = tid & 1;
         bool ok = true;
         for (int64_t c0 = 0; c0 < total && ok; c0 += kLook) {
 #pragma unroll
@@ -377,17 +438,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (c < total && ok) {
                     const int s = int(c % kRing);
                     const uint32_t use = uint32_t(c / kRing);
-                    if (!bar_wait(&S->empty[s], (use & 1) ^ 1, t.err, 11)) {
-                        ok = false;
-                    } else {
+                    ok = __all_sync(0xffffffffu, bar_wait(&S->empty[s], (use & 1) ^ 1, t.err, 11, t.wait_ns));
+                    if (ok) {
                         unsigned char* sb = ring + s * kStageBytes;
 #pragma unroll
-                        for (int j = 0; j < kPerThread; ++j) {
-                            const float2 v = buf[u][j];
-                            const float bx = tf32_rn(v.x), by = tf32_rn(v.y);
-                            *reinterpret_cast<float2*>(sb + pos[j]) = make_float2(bx, by);
-                            *reinterpret_cast<float2*>(sb + kRows * 128 + pos[j]) =
-                                make_float2(tf32_rn(v.x - bx), tf32_rn(v.y - by));
+                        for (int j = 0; j < kPerThread; ++j) *reinterpret_cast<float2*>(sb + pos[j]) = buf[u][j];
+                        bar_arrive(&S->rawb[s]);
+                        ok = __all_sync(0xffffffffu, bar_wait(&S->rawb[s], use & 1, t.err, 19, t.wait_ns));
+                    }
+                    if (ok) {
+                        unsigned char* sb = ring + s * kStageBytes;
+                        // (values are read twice rather than held: the
+                        // registers hold the loads in flight)
+                        float m = 0.f;
+#pragma unroll 1
+                        for (int i = 0; i < 4; ++i)
+                            m = fmaxf(m, absmax4(*reinterpret_cast<const float4*>(
+                                             sb + swz(uint32_t(prow * 128 + phalf * 64 + 16 * i)))));
+                        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+                        const float cg = grid_c(m, t.split_bits);
+#pragma unroll 1
+                        for (int i = 0; i < 4; ++i) {
+                            const uint32_t o = swz(uint32_t(prow * 128 + phalf * 64 + 16 * i));
+                            float4 b, sm4;
+                            split4(*reinterpret_cast<const float4*>(sb + o), cg, b, sm4);
+                            *reinterpret_cast<float4*>(sb + o) = b;
+                            *reinterpret_cast<float4*>(sb + kRows * 128 + o) = sm4;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         bar_arrive(&S->full[s]);
@@ -402,18 +478,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(kRows >> 3) << 17) |
                                    (uint32_t(kM >> 4) << 24);
-            bool ok = bar_wait(&S->wready, 0, t.err, 12);
+            bool ok = bar_wait(&S->wready, 0, t.err, 12, t.wait_ns);
+            const bool four = t.split_terms == 4;
             fence_after();
             uint32_t it = 0, tc = 0;
             for (int64_t tile = t_first; tile < t_end && ok; tile += t_step, ++tc) {
                 const uint32_t b = 0, ub = tc;  // one accumulator pair (TMEM is full)
-                if (!bar_wait(&S->tempty[b], (ub & 1) ^ 1, t.err, 13)) break;
+                if (!bar_wait(&S->tempty[b], (ub & 1) ^ 1, t.err, 13, t.wait_ns)) break;
                 fence_after();
                 const uint32_t d_big = tmem + 256, d_small = d_big + kRows;
                 for (int ch = 0; ch < nch; ++ch, ++it) {
                     const int s = int(it % kRing);
                     const uint32_t use = it / kRing;
-                    if (!bar_wait(&S->full[s], use & 1, t.err, 14)) { ok = false; break; }
+                    if (!bar_wait(&S->full[s], use & 1, t.err, 14, t.wait_ns)) { ok = false; break; }
                     fence_after();
                     const uint32_t sb = smem_u32(ring + s * kStageBytes), ss = sb + kRows * 128;
 #pragma unroll
@@ -423,6 +500,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mma_ts(d_big, w_big + kc, sdesc(sb + kb), idesc, (ch | ks) != 0);
                         mma_ts(d_small, w_small + kc, sdesc(sb + kb), idesc, (ch | ks) != 0);
                         mma_ts(d_small, w_big + kc, sdesc(ss + kb), idesc, 1);
+                        if (four) mma_ts(d_small, w_small + kc, sdesc(ss + kb), idesc, 1);
                     }
                     mma_commit(&S->empty[s]);
                 }
@@ -430,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma_commit(&S->tfull[b]);
             }
             mma_commit(&S->drain);
-            bar_wait(&S->drain, 0, t.err, 15);
+            bar_wait(&S->drain, 0, t.err, 15, t.wait_ns);
         }
         __syncwarp();
     } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
@@ -460,22 +538,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (live)
                 for (int i = 0; i < t.nbn; ++i)
                     if ((n >> i) & 1) noff |= int64_t(1) << t.bpn[i];
+            // value kp of this W^T row: Re / Im of B[k][n] with the sign of
+            // the real expansion (0 for padding rows)
+            auto wval = [&](int kp) {
+                const int k = kp >> 1, apart = kp & 1;
+                if (!live) return 0.f;
+                int64_t off = noff;
+                for (int b = 0; b < t.nbk; ++b)
+                    if ((k >> b) & 1) off |= int64_t(1) << t.bpk[b];
+                const float2 bv = B[off];
+                return cpart == 0 ? (apart == 0 ? bv.x : -bv.y) : (apart == 0 ? bv.y : bv.x);
+            };
+            // the row's grid: its largest magnitude over all of K (32 loads in
+            // flight per step)
+            float wm = 0.f;
+            for (int c0 = 0; c0 < t.K2; c0 += 32) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) wm = fmaxf(wm, fabsf(wval(c0 + i)));
+            }
+            const float cw = grid_c(wm, t.split_bits);
             for (int c0 = 32 * half; c0 < t.K2; c0 += 32 * kShares) {
                 float vb[32], vs[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int kp = c0 + i, k = kp >> 1, apart = kp & 1;
-                    float w = 0.f;
-                    if (live) {
-                        int64_t off = noff;
-                        for (int b = 0; b < t.nbk; ++b)
-                            if ((k >> b) & 1) off |= int64_t(1) << t.bpk[b];
-                        const float2 bv = B[off];
-                        w = cpart == 0 ? (apart == 0 ? bv.x : -bv.y) : (apart == 0 ? bv.y : bv.x);
-                    }
-                    vb[i] = tf32_rn(w);
-                    vs[i] = tf32_rn(w - vb[i]);
-                }
+                for (int i = 0; i < 32; ++i) split_on(wval(c0 + i), cw, vb[i], vs[i]);
                 const uint32_t lanes = uint32_t(q * 32) << 16;
                 tm_st32(w_big + lanes + uint32_t(c0), vb);
                 tm_st32(w_small + lanes + uint32_t(c0), vs);
@@ -542,13 +627,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // leave the others blocked)
         auto epi_sync = [&]() {
             bar_arrive(&S->epi);
-            const bool ok = bar_wait(&S->epi, ep & 1, t.err, 17);
+            const bool ok = bar_wait(&S->epi, ep & 1, t.err, 17, t.wait_ns);
             ++ep;
             return ok;
         };
         for (int64_t tile = t_first; tile < t_end; tile += t_step, ++tc) {
             const uint32_t b = 0, ub = tc;
-            const bool got = bar_wait(&S->tfull[b], ub & 1, t.err, 16);
+            const bool got = bar_wait(&S->tfull[b], ub & 1, t.err, 16, t.wait_ns);
             if (!__all_sync(0xffffffffu, got)) break;
             fence_after();
             // grouped mode: the next tile of this CTA needs its group's W^T,
@@ -653,12 +738,8 @@ static_assert(offsetof(Sm2, rlo) % 16 == 0, "row table read as int4");
 static_assert(sizeof(Sm2) % 8 == 0 && tc2_smem<true>() <= 232448 && tc2_smem<false>() <= 232448,
               "tensor-memory contraction exceeds the shared memory of one CTA");
 
-cudaError_t prepare_tc1();
-
 cudaError_t prepare_tc_kernels() {
-    cudaError_t e = prepare_tc1();
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_gemm2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<true>()));
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<true>()));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tc_gemm2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc2_smem<false>()));
     if (e != cudaSuccess) return e;

@@ -344,6 +344,7 @@ def test_cross_slice_reuse_counts(lib):
     for off in (0, 1):
         o = B.xeb_default_opts()
         o.reserved[7] = off
+        o.fold_legs = -1   # every contraction on the device (folding has its own test)
         plan = B.xeb_plan_create(circ, bits, slices=sliced, opts=o)
         try:
             st = B.xeb_plan_stats(plan)
@@ -464,5 +465,71 @@ def test_new_entry_points_reject_bad_arguments(lib):
         off, el, mk = B.xeb_plan_buffers(plan)
         assert len(off) == 2 * len(B.xeb_network_leaves(circ)[0]) - 1
         assert np.all(el > 0) and np.all(off >= 0) and np.all(mk == 0xFFFFFFFF)   # unsliced: no reuse
+    finally:
+        B.xeb_plan_destroy(plan)
+
+
+def _foldable(plan, circ, sliced, max_legs=16):
+    """Nodes that constant folding takes, walked in plain Python: a subtree
+    qualifies when no leaf in it carries an output bit or a sliced leg and no
+    tensor in it has more than max_legs legs; the qualifying internal nodes
+    whose parent does not qualify are folded with their whole subtree."""
+    tree, _ = B.xeb_plan_tree(plan)
+    out_bits, legs = B.xeb_network_leaves(circ)
+    L = len(legs)
+    ok = [len(out_bits[j]) == 0 and not any(l in sliced for l in legs[j]) and len(legs[j]) <= max_legs
+          for j in range(L)]
+    kids, parent = [], {}
+    for i, (a, b) in enumerate(tree):
+        ca = -1 - a if a < 0 else L + a
+        cb = -1 - b if b < 0 else L + b
+        kids.append((ca, cb))
+        parent[ca] = parent[cb] = L + i
+        nd = B.xeb_plan_node(plan, i)
+        ok.append(ok[ca] and ok[cb] and nd["a"] == nd["b"] and nd["n_legs"] <= max_legs)
+    roots = [v for v in range(L, L + len(tree) - 1) if ok[v] and not ok[parent[v]]]
+    inside = 0
+    for r in roots:
+        stack = [r]
+        while stack:
+            u = stack.pop()
+            inside += 1
+            if u >= L:
+                stack.extend(kids[u - L])
+    return roots, inside
+
+
+@pytest.mark.parametrize("sliced_idx", [(), (3, 17, 40, 55)])
+def test_constant_folding_counts(lib, sliced_idx):
+    """Subtrees that depend on no output bit and no sliced leg are folded on
+    the host: the plan folds exactly the subtrees a plain walk of the rule
+    finds, and a step launches every other contraction (all slices: with
+    cross-slice reuse off, n_gemm_ops minus the folded internal nodes per
+    slice)."""
+    circ = inputs.random_grid_circuit(3, 4, 8, 4545)
+    bits = inputs.uniform_bitstrings(12, 60, 4646)
+    net = network.fused_network(circ)
+    bonds = sorted({l for leaf in net.leaves for l in leaf.legs})
+    sliced = [bonds[i] for i in sliced_idx]
+    o = B.xeb_default_opts()
+    o.reserved[7] = 1
+    plan = B.xeb_plan_create(circ, bits, slices=sliced or None, opts=o)
+    try:
+        st = B.xeb_plan_stats(plan)
+        roots, inside = _foldable(plan, circ, sliced)
+        assert st["n_fold_roots"] == len(roots) and len(roots) > 0
+        assert st["n_folded"] == inside
+        # a folded subtree of r internal nodes holds r + 1 leaves
+        folded_internal = (inside - len(roots)) // 2
+        _, nc = B.xeb_plan_step_flops(plan)
+        assert nc == (st["n_gemm_ops"] - folded_internal) * st["n_slices"]
+    finally:
+        B.xeb_plan_destroy(plan)
+    o.fold_legs = -1
+    plan = B.xeb_plan_create(circ, bits, slices=sliced or None, opts=o)
+    try:
+        st = B.xeb_plan_stats(plan)
+        assert st["n_folded"] == 0 and st["n_fold_roots"] == 0
+        assert B.xeb_plan_step_flops(plan)[1] == st["n_gemm_ops"] * st["n_slices"]
     finally:
         B.xeb_plan_destroy(plan)

@@ -36,10 +36,10 @@ def test_chunked_matches_statevec_and_one_plan(precision, chunk):
     print("chunk %d precision %d: max rel err %.2e, |dF| %.2e" % (chunk, precision, err.max(), abs(F - F_ref)))
     assert err.max() < 1e-5
     assert amps[5] == amps[11]
-    assert abs(F - F_ref) < (1e-6 if precision == B.XEB_PREC_FP32 else 4e-5)
+    assert abs(F - F_ref) < 1e-6
     assert abs(m1 - (F + 1)) < 1e-12
     p = np.abs(ref) ** 2 * 2.0 ** 20
     assert abs(m2 - np.mean(p ** 2)) < 1e-4 * np.mean(p ** 2)
     _, F1, plan = run(circ, bits, precision=precision, opts=o)
     plan.close()
-    assert abs(F - F1) < (1e-6 if precision == B.XEB_PREC_FP32 else 4e-5)
+    assert abs(F - F1) < 1e-6

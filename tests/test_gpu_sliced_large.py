@@ -98,7 +98,7 @@ def test_grid5x8_sliced_plan_matches_oracle(precision):
     err = rel_err(amps, ref, 40)
     print("40q k=200: %d sliced legs, max rel err %.3e, |dF| %.3e" % (st["n_sliced"], err.max(), abs(F - F_ref)))
     assert err.max() < 1e-5
-    assert abs(F - xeb.fidelity(ref, 40)) < (1e-6 if precision == B.XEB_PREC_FP32 else 4e-5)
+    assert abs(F - xeb.fidelity(ref, 40)) < 1e-6
     plan.close()
 
 
@@ -186,14 +186,11 @@ def test_grid6x9m1_split_precision_matches_fp64_on_gpu():
     ref_plan.close()
     scale = np.maximum(np.abs(r), np.sqrt(np.mean(np.abs(r) ** 2)))
     d = np.abs(a - r) / scale
-    # mean relative shrink: the tensor cores' truncating FP32 accumulation
-    # pulls every contraction's result slightly towards zero
+    # mean relative shrink (a bias of the split arithmetic would show here)
     shrink = -np.mean(np.real(np.conj(r) * (a - r))) / np.mean(np.abs(r) ** 2)
     print("53q m=14, slice %d of %d: max rel diff %.3e, mean shrink %.2e" % (int(ids[0]), st["n_slices"], d.max(), shrink))
     assert np.all(np.isfinite(a)) and np.abs(r).max() > 0
-    # measured 1.0e-5 on a GB300: the per-amplitude target of 1e-5 is just
-    # reached at this depth; the bound leaves room for that measurement only
-    assert d.max() < 1.5e-5
+    assert d.max() < 1e-5
 
 
 @pytest.mark.parametrize("precision", [B.XEB_PREC_FP32, B.XEB_PREC_TF32X3])
