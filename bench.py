@@ -134,7 +134,8 @@ from paper_2108_05665_gb300.dist import barrier, max_over_ranks  # noqa: E402
 
 def cpu_oracle_sample(circ, target_s=15.0):
     """Time the FP64 state-vector oracle on the first gates of the circuit
-    (full 2^n state) and extrapolate to the whole circuit."""
+    (full 2^n state) and extrapolate to the whole circuit; returns
+    (extrapolated full-circuit seconds, gates run, all gates, seconds timed)."""
     from oracle import statevec
     gates = circ.gates
     g = 8
@@ -149,7 +150,16 @@ def cpu_oracle_sample(circ, target_s=15.0):
         g = min(len(gates), int(g * max(2.0, target_s / max(dt, 1e-3) * 0.5)))
     # per-gate cost: the 1q / 2q passes are both one sweep over the state
     t_full = dt * len(gates) / g
-    return t_full, g, len(gates)
+    return t_full, g, len(gates), dt
+
+
+def cpu_oracle_full(circ, bits):
+    """One full FP64 state-vector run of the circuit plus the gather of the
+    bitstrings' amplitudes, timed on the host cores."""
+    from oracle import statevec
+    t0 = time.perf_counter()
+    statevec.amplitudes(circ, bits)
+    return time.perf_counter() - t0
 
 
 def reference_arm(args):
@@ -160,21 +170,26 @@ def reference_arm(args):
     circ = w.circuit()
     from oracle import statevec
     statevec.build()
-    times = []
+    full, sample = [], []
     for _ in range(args.warmup + args.steps):
-        t_full, g, G = cpu_oracle_sample(circ, target_s=args.ref_seconds)
-        times.append(t_full)
-    times = times[args.warmup:]
-    t = statistics.median(times)
+        t_full, g, G, dt = cpu_oracle_sample(circ, target_s=args.ref_seconds)
+        full.append(t_full)
+        sample.append(dt)
+    full, sample = full[args.warmup:], sample[args.warmup:]
+    t = statistics.median(full)
     value = w.k / t
     cores = os.cpu_count()
+    # a step is the timed sample (ms_per_step is what each step took); the
+    # amplitudes/s value extrapolates it to the whole circuit
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(sample) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "desc": workload_desc(w)},
+            "extrapolated_full_circuit_ms": t * 1e3,
             "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
-                             "sample": "FP64 state-vector oracle on the first %d of %d gates of the circuit "
-                                       "(full 2^%d state), extrapolated linearly to all gates" % (g, G, w.n_qubits)},
+                             "sample": "each step: the FP64 state-vector oracle on the first %d of %d gates of the "
+                                       "circuit (full 2^%d state, %.1f s); amplitudes/s extrapolated linearly to all "
+                                       "gates" % (g, G, w.n_qubits, statistics.median(sample))},
             "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -206,6 +221,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="cpu_baseline: time one full FP64 state-vector run (about two minutes at 30 qubits) "
+                         "instead of the bounded sample")
+    ap.add_argument("--no-fp32-arm", action="store_true",
+                    help="skip the plain FP32 path's step (timed after the main one, same workload)")
     ap.add_argument("--eager", action="store_true",
                     help="launch the step kernel by kernel instead of replaying one captured CUDA graph")
     ap.add_argument("--split-bits", type=int, default=0,
@@ -415,13 +435,55 @@ def main():
                     for kname, v in prof.items()},
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and w.name == WORKLOAD:
-        t_full, g, G = cpu_oracle_sample(circ)
-        line["cpu_baseline"] = {"value": k / t_full, "unit": "amplitudes/s", "cores": os.cpu_count(),
-                                "kind": "oracle",
-                                "sample": "FP64 state-vector oracle on the first %d of %d gates (full 2^%d state), "
-                                          "extrapolated linearly to the whole circuit" % (g, G, w.n_qubits)}
+    if frac >= 1.0 and w.name == WORKLOAD:
+        # accuracy of this run against the oracle's stored FP64 amplitudes
+        z = np.load(FIXTURE)
+        ref = z["amplitudes"]
+        a = out.cpu().numpy().view(np.complex128)
+        err = np.abs(a - ref) / np.maximum(np.abs(ref), 2.0 ** (-w.n_qubits / 2))
+        line["accuracy"] = {"F_ref": float(z["F"]), "abs_dF": abs(F - float(z["F"])),
+                            "max_amp_err": float(err.max()),
+                            "mean_shrink": float(-np.mean(np.real(np.conj(ref) * (a - ref))) / np.mean(np.abs(ref) ** 2)),
+                            "criterion": "|a - a_ref| / max(|a_ref|, 2^(-n/2)) <= 1e-5, |F - F_ref| <= 1e-6"}
     plan.close()
+    if prec == B.XEB_PREC_TF32X3 and not args.no_fp32_arm and frac >= 1.0 and chosen is None:
+        # the plain FP32 path on the same workload: same planner, FP32 SIMT
+        # complex FMA for every contraction (its own tree from the planner)
+        o32 = B.xeb_default_opts()
+        for f in ("planner", "block_qubits", "group_leaves", "mem_budget", "fold_legs"):
+            setattr(o32, f, getattr(o, f))
+        o32.reserved[2] = o.reserved[2]
+        o32.precision = B.XEB_PREC_FP32
+        p32 = B.Plan(circ, bits, opts=o32).bind()
+        def step32():
+            B.xeb_set_bitstrings(p32.handle, dev_bits.data_ptr(), k, sp)
+            B.xeb_amplitudes(p32.handle, out.data_ptr(), sp)
+        for _ in range(args.warmup):
+            step32()
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step32()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = max_over_ranks(ev0.elapsed_time(ev1), world) / args.steps
+        F32, _, _ = B.xeb_fidelity(p32.handle, sp)
+        p32.close()
+        line["fp32_arm"] = {"ms_per_step": ms32, "value": world * k / (ms32 / 1e3), "unit": "amplitudes/s",
+                            "F": F32, "planner": ["given", "greedy", "sweep", "anneal"][st["planner_used"]]}
+        line["speedup_vs_fp32"] = ms32 / ms_step
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and w.name == WORKLOAD:
+        if args.cpu_full:
+            t_full = cpu_oracle_full(circ, bits)
+            sample = "one full FP64 state-vector run of all %d gates (2^%d state) + gather, timed" % (
+                len(circ.gates), w.n_qubits)
+        else:
+            t_full, g, G, dt = cpu_oracle_sample(circ)
+            sample = ("FP64 state-vector oracle on the first %d of %d gates (full 2^%d state, %.1f s timed), "
+                      "extrapolated linearly to the whole circuit" % (g, G, w.n_qubits, dt))
+        line["cpu_baseline"] = {"value": k / t_full, "unit": "amplitudes/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -290,9 +290,24 @@ xeb_status xeb_amplitudes(struct xeb_plan_s* plan, double* out_dev, uintptr_t st
  * next xeb_amplitudes call recaptures its graph. */
 xeb_status xeb_set_slice_subset(struct xeb_plan_s* plan, double frac, uint64_t seed, int64_t* n_chosen);
 
-/* The slice values the loop runs, in loop order (the subset's, else all
- * 0 .. 2^|S|-1); ids needs room for the count xeb_set_slice_subset returned
- * (2^|S| without a subset).  Bit b of a value is the value of sliced leg b in
+/* Restrict the slice loop to a contiguous block of slice values, for ranks
+ * that share one sum over slices (App. A, "Slicing": the values of the sliced
+ * legs are independent terms, contracted apart and added at the end).  The
+ * loop runs positions lo .. hi-1 of the list xeb_set_slice_subset(frac, seed)
+ * would choose (frac >= 1: all 2^|S| values in counting order), in that order;
+ * xeb_amplitudes then writes the FP64 partial sums over those values (not
+ * amplitudes; the ranks' partial sums add up to the amplitudes, and an empty
+ * block gives zeros).  Blocks [lo_r, hi_r) that tile [0, n) give every value
+ * to exactly one rank.  *n_chosen (may be NULL) receives hi - lo; XEB_EINVAL
+ * for frac <= 0, lo < 0, hi < lo, hi beyond the list or a block above 2^26
+ * values.  Host only; the next xeb_amplitudes call recaptures its graph. */
+xeb_status xeb_set_slice_block(struct xeb_plan_s* plan, double frac, uint64_t seed, int64_t lo, int64_t hi,
+                               int64_t* n_chosen);
+
+/* The slice values the loop runs, in loop order (the block's or the
+ * subset's, else all 0 .. 2^|S|-1); ids needs room for the count
+ * xeb_set_slice_block / xeb_set_slice_subset returned (2^|S| without
+ * either).  Bit b of a value is the value of sliced leg b in
  * the order xeb_plan_tree reports the sliced legs. */
 xeb_status xeb_plan_slice_ids(const struct xeb_plan_s* plan, int64_t* ids);
 
@@ -403,20 +418,6 @@ xeb_status xeb_plan_op_layout(const struct xeb_plan_s* plan, int op_index, int32
 xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* launches, double* flops,
                                  double* bytes);
 
-/* Linear XEB of k complex128 amplitudes already in device memory (amps_dev,
- * 2*k doubles): writes F, the mean of 2^n p and the mean of (2^n p)^2 to
- * out_dev (3 doubles, device) on `stream`, asynchronously, and allocates
- * nothing.  The paper has no counterpart.  It exists for callers that cannot
- * allocate device memory: a process whose device memory belongs to its own
- * pool allocator (cudaMalloc there fails or competes with the pool), or a
- * latency-critical caller that cannot take the implicit device
- * synchronisation of an allocation.  Its block partial sums live in a fixed
- * array inside the library (64 KiB on every device that loads the library,
- * held until the process exits), which limits k to 16,777,216; larger k
- * returns XEB_EINVAL.  The first call on a device looks up that array's
- * device address (with the device current); make that first call before any
- * stream capture.  All calls share the array, so calls whose kernels overlap
- * on the GPU race. */
 /* ---- learned cost model ------------------------------------------------
  * Candidates of the planner for a circuit and bitstring set: every tree the
  * planner would weigh (greedy restarts, sweep family) with the slice set its
@@ -461,6 +462,23 @@ xeb_status xeb_mlp_train_step(struct xeb_mlp_s* mlp, const float* x_dev, const f
  * `stream`.  n_changed (may be NULL): contractions whose form changed. */
 xeb_status xeb_plan_autotune(struct xeb_plan_s* plan, int reps, uintptr_t stream, int32_t* n_changed);
 
+/* Linear XEB of k complex128 amplitudes already in device memory (amps_dev,
+ * 2*k doubles): writes F, the mean of 2^n p and the mean of (2^n p)^2 to
+ * out_dev (3 doubles, device) on `stream`, asynchronously, and allocates
+ * nothing.  The paper has no counterpart.  It exists for callers that cannot
+ * allocate device memory: a process whose device memory belongs to its own
+ * pool allocator (cudaMalloc there fails or competes with the pool), or a
+ * latency-critical caller that cannot take the implicit device
+ * synchronisation of an allocation.  Its block partial sums live in a fixed
+ * array inside the library (64 KiB on every device that loads the library,
+ * held until the process exits), which limits k to 16,777,216; larger k
+ * returns XEB_EINVAL.  The first call on a device looks up that array's
+ * device address (with the device current); make that first call before any
+ * stream capture.  All calls share the array, so calls whose kernels overlap
+ * on the GPU race.  amps_dev must be 16-byte aligned (each amplitude is read as
+ * one 16-byte value; a torch complex128 tensor's storage is); a pointer that is
+ * not is refused with XEB_EINVAL before anything is launched, and so are NULL
+ * pointers and n_qubits outside [1, 64]. */
 xeb_status xeb_linear_xeb_noalloc(const double* amps_dev, size_t k, int n_qubits, double* out_dev,
                                   uintptr_t stream);
 

@@ -122,6 +122,8 @@ _PROTOS = {
                                               ctypes.c_void_p]),
     "xeb_set_slice_subset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64,
                                             ctypes.POINTER(ctypes.c_int64)]),
+    "xeb_set_slice_block": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "xeb_plan_slice_ids": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "xeb_plan_create_batched": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), _u64p, ctypes.c_size_t, ctypes.c_uint64,
                                                ctypes.POINTER(xeb_tree), ctypes.POINTER(xeb_slices),
@@ -364,6 +366,14 @@ def xeb_set_slice_subset(plan, frac: float, seed: int) -> int:
     """Run only a seeded subset of the slice values (partial sums); returns its size."""
     n = ctypes.c_int64()
     _check(load().xeb_set_slice_subset(plan, float(frac), int(seed), ctypes.byref(n)))
+    return n.value
+
+
+def xeb_set_slice_block(plan, lo: int, hi: int, frac: float = 1.0, seed: int = 0) -> int:
+    """Run positions lo .. hi-1 of the slice list (all values, or a seeded
+    subset when frac < 1): partial sums for one rank's block; returns hi - lo."""
+    n = ctypes.c_int64()
+    _check(load().xeb_set_slice_block(plan, float(frac), int(seed), int(lo), int(hi), ctypes.byref(n)))
     return n.value
 
 

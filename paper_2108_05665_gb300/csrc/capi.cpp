@@ -356,7 +356,8 @@ struct xeb_plan_s {
             t_partials = 0, t_result = 0, t_err = 0, t_sort = 0, t_memo = 0;
     size_t memo_bytes = 0;
     std::vector<int> choice;   // per op: CH_AUTO or the autotuner's form
-    std::vector<int64_t> slice_ids;  // seeded subset of slice values (empty: all)
+    bool slice_all = true;           // the loop runs every slice value in counting order
+    std::vector<int64_t> slice_ids;  // else these slice values, in this order (possibly none)
     int n_sms = 152;
     int64_t tables_bytes = 0;
     std::vector<xebk::TrieDesc> trie;
@@ -1691,12 +1692,12 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
     double2* acc = reinterpret_cast<double2*>(tables + p->t_acc);
     const int64_t kv_root = an.nodes.back().kv;
     XEB_CUDA(cudaMemsetAsync(acc, 0, size_t(kv_root << p->w) * 16, st));
-    const int64_t n_run = p->slice_ids.empty() ? int64_t(1) << p->sliced.size() : int64_t(p->slice_ids.size());
+    const int64_t n_run = p->slice_all ? int64_t(1) << p->sliced.size() : int64_t(p->slice_ids.size());
     const auto* ldesc = reinterpret_cast<const xebk::LeafDesc*>(tables + p->t_leaf_desc);
     const double es = double(sizeof(T));
     int64_t s_prev = 0;
     for (int64_t si = 0; si < n_run; ++si) {
-        const int64_t s = p->slice_ids.empty() ? si : p->slice_ids[size_t(si)];
+        const int64_t s = p->slice_all ? si : p->slice_ids[size_t(si)];
         const uint32_t changed = uint32_t(s ^ s_prev);   // slice bits that moved (unused for si = 0)
         s_prev = s;
         {
@@ -1940,43 +1941,77 @@ extern "C" xeb_status xeb_amplitudes(xeb_plan_s* p, double* out_dev, uintptr_t s
     return s;
 }
 
+namespace {
+// The first max(1, round(frac 2^S)) draws of a partial Fisher-Yates shuffle of
+// 0 .. 2^S - 1 driven by splitmix64 from `seed` (see xeb_set_slice_subset);
+// empty for frac >= 1 (all values).
+xeb_status subset_ids(int S, double frac, uint64_t seed, std::vector<int64_t>& ids) {
+    ids.clear();
+    if (!(frac > 0)) return fail(XEB_EINVAL, "slice subset fraction must be > 0");
+    const int64_t n = int64_t(1) << S;
+    if (frac >= 1.0) return XEB_OK;
+    const int64_t cnt = std::max<int64_t>(1, std::llround(frac * double(n)));
+    if (cnt > (int64_t(1) << 26)) return fail(XEB_EINVAL, "slice subset above 2^26 values");
+    // partial Fisher-Yates over 0..n-1 with the swapped positions kept sparse
+    std::unordered_map<int64_t, int64_t> moved;
+    auto at = [&](int64_t i) {
+        auto it = moved.find(i);
+        return it == moved.end() ? i : it->second;
+    };
+    uint64_t x = seed;
+    for (int64_t j = 0; j < cnt; ++j) {
+        x += 0x9e3779b97f4a7c15ULL;  // splitmix64
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        z ^= z >> 31;
+        const int64_t r = j + int64_t(z % uint64_t(n - j));
+        const int64_t vj = at(j), vr = at(r);
+        moved[r] = vj;
+        ids.push_back(vr);
+    }
+    return XEB_OK;
+}
+}  // namespace
+
 extern "C" xeb_status xeb_set_slice_subset(xeb_plan_s* p, double frac, uint64_t seed, int64_t* n_chosen) {
     if (!p) return fail(XEB_EINVAL, "plan is NULL");
-    if (!(frac > 0)) return fail(XEB_EINVAL, "slice subset fraction must be > 0");
-    const int64_t n = int64_t(1) << p->sliced.size();
     std::vector<int64_t> ids;
-    if (frac < 1.0) {
-        const int64_t cnt = std::max<int64_t>(1, std::llround(frac * double(n)));
-        if (cnt > (int64_t(1) << 26)) return fail(XEB_EINVAL, "slice subset above 2^26 values");
-        // partial Fisher-Yates over 0..n-1 with the swapped positions kept sparse
-        std::unordered_map<int64_t, int64_t> moved;
-        auto at = [&](int64_t i) {
-            auto it = moved.find(i);
-            return it == moved.end() ? i : it->second;
-        };
-        uint64_t x = seed;
-        for (int64_t j = 0; j < cnt; ++j) {
-            x += 0x9e3779b97f4a7c15ULL;  // splitmix64
-            uint64_t z = x;
-            z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-            z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-            z ^= z >> 31;
-            const int64_t r = j + int64_t(z % uint64_t(n - j));
-            const int64_t vj = at(j), vr = at(r);
-            moved[r] = vj;
-            ids.push_back(vr);
-        }
-    }
+    const xeb_status st = subset_ids(int(p->sliced.size()), frac, seed, ids);
+    if (st != XEB_OK) return st;
+    p->slice_all = ids.empty();
     p->slice_ids = std::move(ids);
     drop_graph(p, p->graph_plain);
     for (auto& g : p->graph_prof) drop_graph(p, g);
-    if (n_chosen) *n_chosen = p->slice_ids.empty() ? n : int64_t(p->slice_ids.size());
+    if (n_chosen) *n_chosen = p->slice_all ? int64_t(1) << p->sliced.size() : int64_t(p->slice_ids.size());
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_set_slice_block(xeb_plan_s* p, double frac, uint64_t seed, int64_t lo, int64_t hi,
+                                          int64_t* n_chosen) {
+    if (!p) return fail(XEB_EINVAL, "plan is NULL");
+    std::vector<int64_t> ids;
+    const xeb_status st = subset_ids(int(p->sliced.size()), frac, seed, ids);
+    if (st != XEB_OK) return st;
+    const int64_t total = ids.empty() ? int64_t(1) << p->sliced.size() : int64_t(ids.size());
+    if (lo < 0 || hi < lo || hi > total)
+        return fail(XEB_EINVAL, "slice block [" + std::to_string(lo) + ", " + std::to_string(hi) +
+                                    ") outside the " + std::to_string(total) + " slice values");
+    if (hi - lo > (int64_t(1) << 26)) return fail(XEB_EINVAL, "slice block above 2^26 values");
+    std::vector<int64_t> blk;
+    blk.reserve(size_t(hi - lo));
+    for (int64_t i = lo; i < hi; ++i) blk.push_back(ids.empty() ? i : ids[size_t(i)]);
+    p->slice_all = false;
+    p->slice_ids = std::move(blk);
+    drop_graph(p, p->graph_plain);
+    for (auto& g : p->graph_prof) drop_graph(p, g);
+    if (n_chosen) *n_chosen = hi - lo;
     return XEB_OK;
 }
 
 extern "C" xeb_status xeb_plan_slice_ids(const xeb_plan_s* p, int64_t* ids) {
     if (!p || !ids) return fail(XEB_EINVAL, "plan or ids is NULL");
-    if (p->slice_ids.empty()) {
+    if (p->slice_all) {
         const int64_t n = int64_t(1) << p->sliced.size();
         for (int64_t i = 0; i < n; ++i) ids[i] = i;
     } else {
@@ -2234,14 +2269,14 @@ extern "C" xeb_status xeb_plan_buffers(const xeb_plan_s* p, int64_t* off, int64_
 extern "C" xeb_status xeb_plan_step_flops(const xeb_plan_s* p, double* flops, double* contractions) {
     if (!p) return fail(XEB_EINVAL, "NULL plan");
     const int S = int(p->sliced.size());
-    const int64_t n_run = p->slice_ids.empty() ? int64_t(1) << S : int64_t(p->slice_ids.size());
+    const int64_t n_run = p->slice_all ? int64_t(1) << S : int64_t(p->slice_ids.size());
     double fl = 0, nc = 0;
     for (size_t i = 0; i < p->prog.ops.size(); ++i) {
         const Op& op = p->prog.ops[i];
         if (op.kind != OP_GEMM || p->op_folded[i]) continue;
         const uint32_t e = p->node_mask[size_t(op.node)];
         double times = 0;
-        if (p->slice_ids.empty()) {   // counting order: bit b moves every 2^b slices
+        if (p->slice_all) {   // counting order: bit b moves every 2^b slices
             int low = 0;
             while (low < S && !((e >> low) & 1)) ++low;
             times = low >= S ? 1.0 : std::ldexp(1.0, S - low);

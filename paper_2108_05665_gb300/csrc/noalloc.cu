@@ -106,6 +106,8 @@ xeb_status fail(xeb_status s, const std::string& m) {
 extern "C" xeb_status xeb_linear_xeb_noalloc(const double* amps_dev, size_t k, int n_qubits, double* out_dev,
                                              uintptr_t stream) {
     if (!amps_dev || !out_dev) return fail(XEB_EINVAL, "amplitude and output pointers must be device pointers");
+    if (reinterpret_cast<uintptr_t>(amps_dev) % 16 != 0)
+        return fail(XEB_EINVAL, "amps_dev must be 16-byte aligned (amplitudes are read as 16-byte complex values)");
     if (k == 0) return fail(XEB_EINVAL, "need k >= 1 amplitudes");
     if (k > kNoAllocMaxK)
         return fail(XEB_EINVAL, "k = " + std::to_string(k) + " exceeds the allocation-free limit of " +

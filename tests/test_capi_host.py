@@ -533,3 +533,53 @@ def test_constant_folding_counts(lib, sliced_idx):
         assert B.xeb_plan_step_flops(plan)[1] == st["n_gemm_ops"] * st["n_slices"]
     finally:
         B.xeb_plan_destroy(plan)
+
+
+def test_round_keep_norm_stays_between_neighbours_and_keeps_the_norm(lib):
+    """xeb_round_keep_norm: every value is one of the two floats nearest its
+    input (so each error is below one float spacing), the sum of squares lands
+    within one flip of the exact one and never farther than nearest rounding
+    leaves it, exactly representable inputs stay as they are, and for a
+    tensor of many values the norm error falls far below nearest rounding's.
+    The leaves of the fused network (unitary gate tensors) are the inputs the
+    library feeds it."""
+    rng = np.random.default_rng(7)
+    net = network.fused_network(inputs.random_grid_circuit(3, 4, 8, 11))
+    cases = [np.stack([lf.tensor.real.ravel(), lf.tensor.imag.ravel()], 1).ravel() for lf in net.leaves]
+    cases += [rng.standard_normal(n) * s for n, s in ((7, 0.3), (64, 1.0), (4096, 1e-3))]
+    cases.append(np.array([0.5, -0.25, 1.0, 0.0, 3.0]))   # exactly representable
+    big_gain = []
+    for x in cases:
+        y = B.xeb_round_keep_norm(x).astype(np.float64)
+        rn = x.astype(np.float32).astype(np.float64)
+        lo = np.nextafter(rn.astype(np.float32), np.float32(-np.inf)).astype(np.float64)
+        hi = np.nextafter(rn.astype(np.float32), np.float32(np.inf)).astype(np.float64)
+        # y is the nearest float or the other float on the far side of x
+        assert np.all((y == rn) | ((y == lo) & (rn > x)) | ((y == hi) & (rn < x)))
+        assert np.all(y[rn == x] == x[rn == x])
+        e_keep = abs(np.sum(y * y) - np.sum(x * x))
+        e_rn = abs(np.sum(rn * rn) - np.sum(x * x))
+        assert e_keep <= e_rn + 1e-30
+        step = 2 * np.max(np.abs(x)) * np.max(np.abs(hi - lo)) + 1e-300
+        assert e_keep <= step
+        if x.size >= 64:
+            big_gain.append(e_keep / max(e_rn, 1e-300))
+    assert max(big_gain) < 0.1
+
+
+def test_noalloc_xeb_refuses_bad_arguments_before_any_launch(lib):
+    """The allocation-free XEB checks its arguments on the host before it
+    touches the device: NULL pointers, an amplitude pointer that is not
+    16-byte aligned (amplitudes are read as 16-byte values), k = 0, k beyond
+    the fixed scratch array and n_qubits outside [1, 64] return XEB_EINVAL
+    (these calls run here, where there is no GPU)."""
+    aligned, misaligned = 0x10000, 0x10008
+    bad = [(0, 10, 12, aligned), (aligned, 10, 12, 0), (misaligned, 10, 12, aligned), (aligned, 0, 12, aligned),
+           (aligned, 16777217, 12, aligned), (aligned, 10, 0, aligned), (aligned, 10, 65, aligned)]
+    for a, k, n, o in bad:
+        with pytest.raises(B.XebError) as e:
+            B.xeb_linear_xeb_noalloc(a, k, n, o, 0)
+        assert e.value.status == 1
+    with pytest.raises(B.XebError) as e:
+        B.xeb_linear_xeb_noalloc(misaligned, 10, 12, aligned, 0)
+    assert "16-byte" in str(e.value)
