@@ -292,6 +292,18 @@ def main():
     try:
         if chosen is not None:
             plan = B.Plan(circ, bits, tree=chosen["tree"], slices=chosen["slices"] or None, opts=o)
+        elif world > 1:
+            # every rank runs the same tree and slice set: rank 0 plans, the
+            # others build their plans from its choice
+            import torch.distributed as dist
+            shared = [None]
+            if rank == 0:
+                plan = B.Plan(circ, bits, opts=o)
+                shared = [plan.tree()]
+            dist.broadcast_object_list(shared, src=0)
+            if rank != 0:
+                tree0, sl0 = shared[0]
+                plan = B.Plan(circ, bits, tree=tree0, slices=list(sl0) or None, opts=o)
         else:
             plan = B.Plan(circ, bits, opts=o)
         plan.bind()
@@ -314,22 +326,41 @@ def main():
     n_run = st["n_slices"]
     if args.slices is not None and args.slices < n_run:
         args.slice_frac = args.slices / float(n_run)
+    sub_frac = 1.0
     if args.slice_frac is not None and args.slice_frac < 1.0:
         n_run = B.xeb_set_slice_subset(plan.handle, args.slice_frac, 12345)
         frac = n_run / st["n_slices"]
+        sub_frac = args.slice_frac
+    # N ranks on a sliced plan split its slice list into contiguous blocks
+    # (App. A "Slicing": independent terms); each step ends with one FP64
+    # all-reduce of the k partial amplitudes.  Unsliced plans: replicas.
+    partition = world > 1 and n_run > 1
+    block = None
+    if partition:
+        from paper_2108_05665_gb300.dist import shard_range
+        block = shard_range(n_run, rank, world)
+        B.xeb_set_slice_block(plan.handle, block[0], block[1], sub_frac, 12345)
     tuned = None
     if args.autotune > 0:
         B.xeb_set_bitstrings(plan.handle, dev_bits.data_ptr(), k, sp)
         tuned = B.xeb_plan_autotune(plan.handle, args.autotune, sp)
 
+    xeb_out = torch.empty(3, dtype=torch.float64, device="cuda")
+
     def step():
         B.xeb_set_bitstrings(plan.handle, dev_bits.data_ptr(), k, sp)
         B.xeb_amplitudes(plan.handle, out.data_ptr(), sp)
+        if partition:
+            import torch.distributed as dist
+            dist.all_reduce(out, op=dist.ReduceOp.SUM)   # the one exchange: FP64 partial amplitudes
+            B.xeb_linear_xeb_noalloc(out.data_ptr(), k, w.n_qubits, xeb_out.data_ptr(), sp)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     F, m1, m2 = B.xeb_fidelity(plan.handle, sp)
+    if partition:
+        F = float(xeb_out[0].item())
     # ---- timed region (device-resident inputs) ----
     B.xeb_plan_profile(plan.handle, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -347,21 +378,35 @@ def main():
     ms_total = ev0.elapsed_time(ev1)
     ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    value = world * k * args.steps / (ms_total / 1e3) * frac
+    value = (1 if partition else world) * k * args.steps / (ms_total / 1e3) * frac
     clocks = clk.summary()
     # ---- end-to-end through the host entry point (pinned host buffers) ----
     hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
     ha = torch.empty(2 * k, dtype=torch.float64).pin_memory()
-    B.xeb_run(plan.handle, hb.data_ptr(), k, ha.data_ptr(), sp)
+    hF = torch.empty(3, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        if not partition:
+            return B.xeb_run(plan.handle, hb.data_ptr(), k, ha.data_ptr(), sp)
+        # a rank's block from host bitstrings: copy in, contract, all-reduce,
+        # fold, copy the amplitudes and F out
+        dev_bits.copy_(hb, non_blocking=True)
+        step()
+        ha.copy_(out, non_blocking=True)
+        hF.copy_(xeb_out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return float(hF[0])
+
+    e2e_step()
     barrier(world)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     e_steps = max(1, args.steps // 2)
     for _ in range(e_steps):
-        Fe = B.xeb_run(plan.handle, hb.data_ptr(), k, ha.data_ptr(), sp)
+        Fe = e2e_step()
     torch.cuda.synchronize()
     e_s = max_over_ranks(time.perf_counter() - e0, world)
-    e2e_value = world * k * e_steps / e_s * frac
+    e2e_value = (1 if partition else world) * k * e_steps / e_s * frac
     # ---- roofline of the dominant kernel class ----
     pk, pk_kind = peaks()
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -396,7 +441,8 @@ def main():
     launches_per_step = sum(v["launches"] for v in prof.values()) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong" if partition else "weak",
         "vs_baseline": None, "dtype": {"fp32": "fp32", "tf32x3": "tf32x3"}[args.precision],
         "data": "synthetic",
         "config": {"workload": w.name, "desc": workload_desc(w), "precision": args.precision,
@@ -413,7 +459,10 @@ def main():
                                                                             n_run, st["n_slices"]))
                    if frac < 1.0 else "all",
                    "l2": "no flush: per-step working set (%.1f GB arena) >> 129 MB L2" % (st["arena_bytes"] / 1e9),
-                   "parallelism": "replicas: each rank contracts its own batch" if world > 1 else "1 GPU"},
+                   "parallelism": ("slice partition: rank r runs block %d of %d contiguous blocks of the %d slice "
+                                   "values, then one NCCL all-reduce of the k FP64 partial amplitudes and the XEB "
+                                   "fold" % (rank, world, n_run)) if partition else
+                                  ("replicas: each rank contracts its own batch" if world > 1 else "1 GPU")},
         "complex_tflops": eff_tflops,
         "flops_per_step": step_flops,
         "nodes_kept_across_slices": st["n_reused"],
