@@ -158,7 +158,7 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits, bool tmem_variant) {
     for (int i = 0; i < t.nbn; ++i) t.bpn[i] = int8_t(op.b_pos_n[i]);
     // TMA mode (candidate; the tensor map is encoded at bind): A is a
     // row-major [M][K] matrix and the tile's lowest >= 3 row bits are the
-    // matrix's lowest rows, so a chunk is a few boxes of >= 8 consecutive rows
+    // matrix's lowest rows, so a tile is 16 boxes of 8 consecutive whole rows
     t.tma = 0;
     if (tmem_variant && op.M <= (int64_t(1) << 31)) {
         const int nak = int(op.a_pos_k.size());
@@ -169,6 +169,7 @@ bool tc_tile(const Op& op, xebk::TcDesc& t, int row_bits, bool tmem_variant) {
         while (a < row_bits && tile_rows[a] == a) ++a;
         if (row_major && a >= 3) {
             t.tma = 1;
+            a = 3;
             t.box_log2 = a;
             t.row_shift = nak;
             for (int j = 0; j < (1 << (row_bits - a)); ++j) {
@@ -262,8 +263,10 @@ EncodeTiledFn encode_tiled_fn() {
     return fn;
 }
 
-// Tensor map of a TMA-mode launch's A operand: [M rows][2K floats], boxes of
-// 32 floats (one 128-byte swizzle atom) x 2^box_log2 rows, 128-byte swizzle.
+// Tensor map of a TMA-mode launch's A operand: the row-major [M rows][2K
+// floats] matrix seen as (32 floats of a chunk, row, chunk), boxes of 32
+// floats x 2^box_log2 rows x all 2K/32 chunks, 128-byte swizzle: one box is
+// 2^box_log2 whole rows, laid out chunk-major in shared memory.
 // False (the launch then gathers with plain loads) if the base is not 16-byte
 // aligned or the driver refuses the map.
 bool encode_a_map(const xebk::TcDesc& t, const float2* arena, CUtensorMap& map) {
@@ -271,11 +274,11 @@ bool encode_a_map(const xebk::TcDesc& t, const float2* arena, CUtensorMap& map) 
     if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
     EncodeTiledFn fn = encode_tiled_fn();
     if (!fn) return false;
-    const cuuint64_t dims[2] = {cuuint64_t(t.K2), cuuint64_t(t.M)};
-    const cuuint64_t strides[1] = {cuuint64_t(t.K2) * 4};
-    const cuuint32_t box[2] = {32u, cuuint32_t(1u << t.box_log2)};
-    const cuuint32_t estr[2] = {1u, 1u};
-    return fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(base), dims, strides, box, estr,
+    const cuuint64_t dims[3] = {32u, cuuint64_t(t.M), cuuint64_t(t.n_chunks)};
+    const cuuint64_t strides[2] = {cuuint64_t(t.K2) * 4, 128u};
+    const cuuint32_t box[3] = {32u, cuuint32_t(1u << t.box_log2), cuuint32_t(t.n_chunks)};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }

@@ -64,16 +64,19 @@ constexpr int kProd = 32 * 8;                     // gather mode: 256 producer t
 constexpr int kPerThread = kRows * 16 / kProd;    // gather mode: 8 complex elements per producer per chunk
 constexpr int kLook = 4;                          // gather mode: chunks of loads in flight per producer (registers)
 constexpr int kStageBytes = 2 * kRows * 128;      // operand stage: big + small, 16 KB each
-constexpr int kRawBytes = kRows * 128;            // TMA mode: raw stage, 16 KB
+constexpr int kSmallBytes = kRows * 128;          // TMA mode: stage of one chunk's small parts, 16 KB
 constexpr int kRingGather = 4;                    // operand stages, gather mode
-constexpr int kRingTma = 3;                       // operand stages, TMA mode
-constexpr int kRaw = 4;                           // raw stages, TMA mode (64 KB of loads in flight)
+constexpr int kRingTma = 2;                       // small-part stages, TMA mode
+constexpr int kRaw = 2;                           // whole-tile buffers, TMA mode
+constexpr int kTileBytes = kRows * 128 * 4;       // TMA mode: one tile, 128 rows x up to 128 floats (64 KB)
 constexpr int kCStride = 128;                     // floats per staged output row (XOR-swizzled columns)
 constexpr uint32_t kTmemCols = 512;
 template <bool kTma>
 __host__ __device__ constexpr int op_stages() { return kTma ? kRingTma : kRingGather; }
 template <bool kTma>
-constexpr size_t ring_bytes() { return (kTma ? size_t(kRaw) * kRawBytes : 0) + size_t(op_stages<kTma>()) * kStageBytes; }
+__host__ __device__ constexpr size_t ring_bytes() {
+    return kTma ? size_t(kRaw) * kTileBytes + size_t(kRingTma) * kSmallBytes : size_t(kRingGather) * kStageBytes;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -122,12 +125,13 @@ __device__ void bar_wait_drain(uint64_t* b, uint32_t par, uint64_t lim) {
 __device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
 }
-// 2-D tiled TMA load (x = floats, y = rows) completing on mbarrier b
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b) {
+// 3-D tiled TMA load (x = floats of a chunk, y = rows, z = chunks) completing
+// on mbarrier b
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* b) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(b))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(b))
         : "memory");
 }
 __device__ __forceinline__ uint32_t swz(uint32_t byte) { return byte ^ (((byte >> 7) & 7u) << 4); }
@@ -164,8 +168,10 @@ __device__ __forceinline__ void split4(float4 v, float c, float4& b, float4& s) 
     split_on(v.z, c, b.z, s.z);
     split_on(v.w, c, b.w, s.w);
 }
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+// shared-memory operand descriptor: K-major, 128-byte swizzle, 8-row groups
+// sbo bytes apart (1024 when the groups are contiguous)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t sbo = 1024) {
+    return uint64_t((saddr & 0x3FFFF) >> 4) | (uint64_t(1) << 16) | (uint64_t(sbo >> 4) << 32) |
            (uint64_t(1) << 46) | (uint64_t(2) << 61);
 }
 // D[tmem] (+)= A[tmem] * B[smem]
@@ -222,6 +228,11 @@ struct Sm2 {
     // staging offset (floats) of tile row r = rlo[r % 32] ^ rhi[r / 32]: the
     // row's base r * kCStride with its column swizzle folded in (linear in r)
     int32_t rlo[32], rhi[kRows / 32];
+    // per result-tile bit i (ascending C order): C increment and staging-slot
+    // XOR; per tile index bit outside the tile: C increment
+    int64_t cinc[16];
+    int32_t sinc[16];
+    int64_t extinc[32];
 };
 
 }  // namespace
@@ -236,10 +247,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kEpiWarp0 = kProdWarps;
     constexpr int kEpiT = 32 * kEpiWarps;
     extern __shared__ __align__(1024) unsigned char raw2[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw2) + 1023) & ~uintptr_t(1023));
-    unsigned char* rawr = sm;                                          // TMA mode: kRaw x 16 KB
-    unsigned char* ring = sm + (kTma ? kRaw * kRawBytes : 0);          // kRing x (big 16 KB | small 16 KB)
-    float* cst = reinterpret_cast<float*>(ring + kRing * kStageBytes);  // kRows x kCStride
+    // 1024-byte aligned base, derived from the shared array by pointer
+    // arithmetic so every pointer below stays a shared-memory pointer
+    unsigned char* sm = raw2 + ((1024u - (smem_u32(raw2) & 1023u)) & 1023u);
+    // TMA mode: kRaw whole-tile buffers (raw values, split in place into the
+    // bigs), then kRingTma stages of one chunk's smalls.  Gather mode: kRing
+    // stages of (big 16 KB | small 16 KB).
+    unsigned char* tbuf = sm;
+    unsigned char* ring = sm + (kTma ? kRaw * kTileBytes : 0);
+    float* cst = reinterpret_cast<float*>(sm + ring_bytes<kTma>());  // kRows x kCStride
     Sm2* S = reinterpret_cast<Sm2*>(cst + kRows * kCStride);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = kGrp ? t.n_groups * t.tpg : t.M / kRows;
@@ -262,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int s = 0; s < kRaw; ++s) {
             bar_init(&S->rfull[s], 1);
-            bar_init(&S->rempty[s], kProdT);
+            bar_init(&S->rempty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(&S->tfull[b], 1);
@@ -281,6 +297,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!((t.st_is_n >> i) & 1) && ((r >> t.st_idx[i]) & 1)) x ^= int(t.st_swz[i]);
         (tid < 32 ? S->rlo[tid] : S->rhi[tid - 32]) = (r * kCStride) ^ (2 * x);
     }
+    if (tid < 16) {
+        const int i = tid;
+        S->cinc[i] = i < t.Tst ? int64_t(1) << t.st_pos[i] : 0;
+        S->sinc[i] = i < t.Tst ? ((((t.st_is_n >> i) & 1) ? (1 << t.st_idx[i]) : (1 << t.st_idx[i]) * (kCStride / 2)) ^
+                                  int(t.st_swz[i]))
+                               : 0;
+    }
+    if (tid >= 32 && tid < 64) {
+        const int i = tid - 32;
+        S->extinc[i] = i < t.n_ext ? int64_t(1) << t.ext_cpos[i] : 0;
+    }
     if (tid == 0) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -297,74 +324,77 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t w_big = tmem, w_small = tmem + 128;
 
     if (kTma && warp < kProdWarps) {
-        // ---------------- TMA mode: split landed raw chunks into the operand ring ----------------
-        // raw and operand stages are 1024-byte aligned, so the 128-byte swizzle
-        // the TMA applied is the layout the MMA reads: the split is a linear
-        // copy.  A 128-byte line is one state row's 32 values of the chunk;
-        // thread tid splits line tid (its maximum is the row's grid), visiting
-        // the line's 16-byte units from (tid & 7) on, so the 8 lanes of each
-        // shared-memory phase touch 8 different bank groups.  The grid is
-        // found as soon as the chunk lands, before waiting for a free operand
-        // stage.
+        // ---------------- TMA mode: split each landed tile, chunk by chunk ----------------
+        // A tile lands as 16 groups of 8 consecutive A rows, each group holding
+        // all of its rows' chunks: group j, chunk c is the 1024-byte swizzle
+        // atom at j * (n_chunks KB) + c KB, 128-byte line per row -- the
+        // layout the MMA reads with an 8-row-group stride of n_chunks KB.
+        // Thread tid splits tile row tid: its line of chunk c gives the row's
+        // grid; the bigs overwrite the raw values in place, the smalls go to a
+        // small-part stage at the same position inside a contiguous tile
+        // (group stride 1 KB).  16-byte units are visited from (tid & 7) on,
+        // so the 8 lanes of each shared-memory phase touch 8 bank groups.
         static_assert(!kTma || kProdT == kRows, "one split thread per tile row");
-        const int64_t total = my_tiles * nch;
-        for (int64_t c = 0; c < total; ++c) {
-            const int s1 = int(c % kRaw), s2 = int(c % kRing);
-            if (!bar_wait(&S->rfull[s1], uint32_t(c / kRaw) & 1, t.err, 20, t.wait_ns)) break;
-            const unsigned char* src = rawr + s1 * kRawBytes + tid * 128;
-            float4 v[8];
-            float m = 0.f;
+        const int gsz = nch * 1024;
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t i = 0; i < my_tiles && ok; ++i) {
+            const int b = int(i & 1);
+            if (!bar_wait(&S->rfull[b], uint32_t(i >> 1) & 1, t.err, 20, t.wait_ns)) break;
+            unsigned char* rowp = tbuf + b * kTileBytes + (tid >> 3) * gsz + (tid & 7) * 128;
+            for (int c = 0; c < nch; ++c, ++g) {
+                const int s2 = int(g & 1);
+                unsigned char* src = rowp + c * 1024;
+                float4 v[8];
+                float m = 0.f;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                v[i] = *reinterpret_cast<const float4*>(src + 16 * ((i + tid) & 7));
-                m = fmaxf(m, absmax4(v[i]));
-            }
-            const float cg = grid_c(m, t.split_bits);
-            if (!bar_wait(&S->empty[s2], (uint32_t(c / kRing) & 1) ^ 1, t.err, 11, t.wait_ns)) break;
-            unsigned char* db = ring + s2 * kStageBytes + tid * 128;
-            unsigned char* ds = db + kRawBytes;
+                for (int i2 = 0; i2 < 8; ++i2) {
+                    v[i2] = *reinterpret_cast<const float4*>(src + 16 * ((i2 + tid) & 7));
+                    m = fmaxf(m, absmax4(v[i2]));
+                }
+                const float cg = grid_c(m, t.split_bits);
+                if (!bar_wait(&S->empty[s2], (uint32_t(g >> 1) & 1) ^ 1, t.err, 11, t.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* ds = ring + s2 * kSmallBytes + (tid >> 3) * 1024 + (tid & 7) * 128;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                float4 b, sm4;
-                split4(v[i], cg, b, sm4);
-                *reinterpret_cast<float4*>(db + 16 * ((i + tid) & 7)) = b;
-                *reinterpret_cast<float4*>(ds + 16 * ((i + tid) & 7)) = sm4;
+                for (int i2 = 0; i2 < 8; ++i2) {
+                    float4 bg, sm4;
+                    split4(v[i2], cg, bg, sm4);
+                    *reinterpret_cast<float4*>(src + 16 * ((i2 + tid) & 7)) = bg;
+                    *reinterpret_cast<float4*>(ds + 16 * ((i2 + tid) & 7)) = sm4;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_arrive(&S->full[s2]);
             }
-            bar_arrive(&S->rempty[s1]);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bar_arrive(&S->full[s2]);
         }
     } else if (kTma && warp == kTmaWarp) {
-        // ---------------- TMA mode: one thread issues the box loads ----------------
+        // ---------------- TMA mode: one thread loads whole tiles ----------------
+        // 16 boxes per tile, each 8 consecutive A rows x all chunks: every box
+        // reads 8 whole rows (8 x n_chunks x 128 contiguous bytes)
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
-            const int64_t total = my_tiles * nch;
-            const int nbox = kRows >> t.box_log2;
-            const int brow = (1 << t.box_log2) * 128;  // bytes of one box in shared memory
+            const int nbox = kRows >> 3;
+            const int gsz = nch * 1024;
             auto ybase = [&](int64_t tile) {
                 int64_t y = 0;
                 for (int i = 0; i < t.n_ext; ++i)
                     if ((tile >> i) & 1) y |= int64_t(1) << (t.ext_apos[i] - t.row_shift);
                 return y;
             };
-            int64_t tile = t_first, c = 0;
-            int cin = 0;
-            int64_t y0 = ybase(tile);
-            for (; c < total; ++c) {
-                const int s = int(c % kRaw);
-                if (!bar_wait(&S->rempty[s], (uint32_t(c / kRaw) & 1) ^ 1, t.err, 18, t.wait_ns)) break;
-                bar_expect_tx(&S->rfull[s], kRawBytes);
-                unsigned char* dst = rawr + s * kRawBytes;
+            int64_t i = 0;
+            for (int64_t tile = t_first; tile < t_end; tile += t_step, ++i) {
+                const int b = int(i & 1);
+                if (!bar_wait(&S->rempty[b], (uint32_t(i >> 1) & 1) ^ 1, t.err, 18, t.wait_ns)) break;
+                bar_expect_tx(&S->rfull[b], uint32_t(kRows * 128 * nch));
+                const int64_t y0 = ybase(tile);
+                unsigned char* dst = tbuf + b * kTileBytes;
                 for (int j = 0; j < nbox; ++j)
-                    tma_load_2d(dst + j * brow, &tmap, kChunk * cin, int(y0 + t.box_y[j]), &S->rfull[s]);
-                if (++cin == nch) {
-                    cin = 0;
-                    tile += t_step;
-                    y0 = tile < t_end ? ybase(tile) : 0;
-                }
+                    tma_load_3d(dst + j * gsz, &tmap, 0, int(y0 + t.box_y[j]), 0, &S->rfull[b]);
             }
             // the CTA must not exit with copies in flight: wait (bounded) for the last ones
-            for (int64_t d = c > kRaw ? c - kRaw : 0; d < c; ++d)
+            for (int64_t d = i > kRaw ? i - kRaw : 0; d < i; ++d)
                 bar_wait_drain(&S->rfull[d % kRaw], uint32_t(d / kRaw) & 1, t.wait_ns);
         }
         __syncwarp();
@@ -492,18 +522,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t use = it / kRing;
                     if (!bar_wait(&S->full[s], use & 1, t.err, 14, t.wait_ns)) { ok = false; break; }
                     fence_after();
-                    const uint32_t sb = smem_u32(ring + s * kStageBytes), ss = sb + kRows * 128;
+                    // big and small operands of this chunk (TMA mode: bigs in the
+                    // tile buffer, 8-row groups n_chunks KB apart)
+                    uint32_t sb, ss, sbo_b;
+                    if constexpr (kTma) {
+                        sb = smem_u32(tbuf + (tc & 1) * kTileBytes + ch * 1024);
+                        ss = smem_u32(ring + s * kSmallBytes);
+                        sbo_b = uint32_t(nch * 1024);
+                    } else {
+                        sb = smem_u32(ring + s * kStageBytes);
+                        ss = sb + kRows * 128;
+                        sbo_b = 1024;
+                    }
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         const uint32_t kc = uint32_t(ch * kChunk + ks * 8);  // TMEM column of this K step
                         const uint32_t kb = ks * 32;                          // byte offset in the swizzle atom
-                        mma_ts(d_big, w_big + kc, sdesc(sb + kb), idesc, (ch | ks) != 0);
-                        mma_ts(d_small, w_small + kc, sdesc(sb + kb), idesc, (ch | ks) != 0);
+                        mma_ts(d_big, w_big + kc, sdesc(sb + kb, sbo_b), idesc, (ch | ks) != 0);
+                        mma_ts(d_small, w_small + kc, sdesc(sb + kb, sbo_b), idesc, (ch | ks) != 0);
                         mma_ts(d_small, w_big + kc, sdesc(ss + kb), idesc, 1);
                         if (four) mma_ts(d_small, w_small + kc, sdesc(ss + kb), idesc, 1);
                     }
                     mma_commit(&S->empty[s]);
                 }
+                if (kTma && ok) mma_commit(&S->rempty[tc & 1]);   // the tile buffer is read
                 if (!ok) break;
                 mma_commit(&S->tfull[b]);
             }
@@ -623,6 +665,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
         }
         const int nlo = 1 << lb, nmid = 1 << (wb - lb);
+        // the middle loop's bits are tile bits 5 + lb .. 4 + wb (at most 6:
+        // Tst <= 16); their increments and those of the tile index bits
+        // outside the tile come from the shared tables (no parameter array
+        // is indexed inside the tile loop)
+        const int jb0 = 5 + lb;
         // bounded sync of the four epilogue warps (an aborting warp cannot
         // leave the others blocked)
         auto epi_sync = [&]() {
@@ -683,18 +730,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     cbase = u0 * t.c_key;
                 }
             }
-            for (int i = 0; i < t.n_ext; ++i)
-                if ((mt >> i) & 1) cbase += int64_t(1) << t.ext_cpos[i];
+            {   // C offset of the tile index bits outside the tile: one bit per lane, summed
+                int64_t xb = ((mt >> lane) & 1) ? S->extinc[lane] : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) xb += __shfl_xor_sync(0xffffffffu, xb, o);
+                cbase += xb;
+            }
             float2* C = arena + t.c_off + cbase;
             const float2* st2 = reinterpret_cast<const float2*>(cst);
             if (e_active && (!kGrp || t.keyed)) {
                 for (int jm = 0; jm < nmid; ++jm) {
                     int64_t gm = gq;
                     int sm2 = sq;
-                    for (int bb = 0; bb < wb - lb; ++bb)
+                    for (int bb = 0; (jm >> bb) != 0; ++bb)
                         if ((jm >> bb) & 1) {
-                            gm += ginc(5 + lb + bb);
-                            sm2 ^= sinc(5 + lb + bb);
+                            gm += S->cinc[jb0 + bb];
+                            sm2 ^= S->sinc[jb0 + bb];
                         }
                     float2 v[8];
 #pragma unroll
@@ -708,10 +759,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int jm = 0; jm < nmid; ++jm) {
                     int64_t gm = gq;
                     int sm2 = sq;
-                    for (int bb = 0; bb < wb - lb; ++bb)
+                    for (int bb = 0; (jm >> bb) != 0; ++bb)
                         if ((jm >> bb) & 1) {
-                            gm += ginc(5 + lb + bb);
-                            sm2 ^= sinc(5 + lb + bb);
+                            gm += S->cinc[jb0 + bb];
+                            sm2 ^= S->sinc[jb0 + bb];
                         }
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
