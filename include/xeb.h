@@ -482,6 +482,17 @@ xeb_status xeb_plan_autotune(struct xeb_plan_s* plan, int reps, uintptr_t stream
 xeb_status xeb_linear_xeb_noalloc(const double* amps_dev, size_t k, int n_qubits, double* out_dev,
                                   uintptr_t stream);
 
+/* Testing aid for the bounded waits (not part of the paper's method): with
+ * enable != 0 every tensor-core contraction of the plan first waits on a
+ * barrier that nothing completes, so that wait runs out after opts.timeout_ms;
+ * the kernel records the timeout in the plan's error word, its threads leave
+ * their loops (copies in flight drained, MMAs finished, tensor memory freed)
+ * and the next xeb_fidelity / xeb_run returns XEB_ETIMEOUT.  enable = 0
+ * restores normal steps (the error word is cleared once it is reported).
+ * Host only; the next xeb_amplitudes call recaptures its graph.  XEB_EINVAL
+ * for a NULL plan. */
+xeb_status xeb_plan_test_wait(struct xeb_plan_s* plan, int enable);
+
 /* Thread-local message of the last failure in this thread. */
 const char* xeb_last_error(void);
 

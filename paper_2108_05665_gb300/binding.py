@@ -81,6 +81,7 @@ class xeb_stats(ctypes.Structure):
 
 _PROTOS = {
     "xeb_default_opts": (None, [ctypes.POINTER(xeb_plan_opts)]),
+    "xeb_plan_test_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "xeb_round_keep_norm": (None, [_dblp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_float)]),
     "xeb_network_info": (ctypes.c_int, [ctypes.POINTER(xeb_circuit), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
@@ -404,6 +405,10 @@ def xeb_plan_keys(plan, node: int, k: int, kv: int, stream: int):
     _check(load().xeb_plan_keys(plan, node, _ptr(key, ctypes.c_int32), _ptr(uL, ctypes.c_int32),
                                 _ptr(uR, ctypes.c_int32), ctypes.c_void_p(stream or None)))
     return key, uL[:kv], uR[:kv]
+
+
+def xeb_plan_test_wait(plan, enable: bool):
+    _check(load().xeb_plan_test_wait(plan, 1 if enable else 0))
 
 
 def xeb_linear_xeb_noalloc(amps_dev_ptr: int, k: int, n_qubits: int, out_dev_ptr: int, stream: int):

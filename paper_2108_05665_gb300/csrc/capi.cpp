@@ -332,6 +332,7 @@ struct xeb_plan_s {
     // and no open leg are evaluated once on the host in FP64 (fold_roots: the
     // largest such subtrees, their values in the root node's stored layout);
     // their leaves and contractions never run on the device
+    int test_wait = 0;                 // xeb_plan_test_wait
     std::vector<char> folded;          // per node: inside a folded subtree
     std::vector<char> op_folded;       // per program op
     std::vector<int> fold_roots;
@@ -1335,6 +1336,7 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
         g.tc.split_bits = p->opts.split_bits > 0 ? p->opts.split_bits : kSplitBitsDefault;
         g.tc.split_terms = p->opts.split_terms > 0 ? p->opts.split_terms : kSplitTermsDefault;
         g.tc.wait_ns = uint64_t(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : kTimeoutMsDefault) * 1000000ull;
+        g.tc.test_wait = p->test_wait;
         std::memset(&g.tmap, 0, sizeof(g.tmap));
     };
     if (op.M == 1 && op.N == 1) {
@@ -2034,6 +2036,10 @@ extern "C" xeb_status xeb_fidelity(xeb_plan_s* p, double* F, double* m1, double*
     XEB_CUDA(cudaMemcpyAsync(res, tables + p->t_result, 32, cudaMemcpyDeviceToHost, st));
     XEB_CUDA(cudaMemcpyAsync(&err, tables + p->t_err, 4, cudaMemcpyDeviceToHost, st));
     XEB_CUDA(cudaStreamSynchronize(st));
+    if (err) {   // reported once: the word is cleared so the plan's next step starts clean
+        XEB_CUDA(cudaMemsetAsync(tables + p->t_err, 0, 4, st));
+        XEB_CUDA(cudaStreamSynchronize(st));
+    }
     if (err & xebk::kErrTimeout)
         return fail(XEB_ETIMEOUT, "a bounded device wait gave up (role " + std::to_string(err & 0xff) + ")");
     if (err) return fail(XEB_EDEVICE, "device key tables disagree with the plan's counts (node " +
@@ -2243,6 +2249,16 @@ extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t strea
     for (auto& g : p->graph_prof) drop_graph(p, g);
     if (n_changed) *n_changed = changed;
     return s;
+}
+
+extern "C" xeb_status xeb_plan_test_wait(xeb_plan_s* p, int enable) {
+    if (!p) return fail(XEB_EINVAL, "NULL plan");
+    p->test_wait = enable != 0;
+    for (GemmLaunch& g : p->gemms)
+        if (g.kernel == GK_TC2) g.tc.test_wait = p->test_wait;
+    drop_graph(p, p->graph_plain);
+    for (auto& g : p->graph_prof) drop_graph(p, g);
+    return XEB_OK;
 }
 
 extern "C" xeb_status xeb_plan_profile(xeb_plan_s* p, int enable) {

@@ -121,6 +121,7 @@ struct TcDesc {
     // 3 (big*big, big*small, small*big) or 4 (+ small*small)
     int split_bits, split_terms;
     uint64_t wait_ns;     // limit of every device-side wait (ns of %globaltimer)
+    int test_wait;        // testing aid: the MMA thread first waits on a barrier nothing completes
     // (tensor-memory variant, TMA mode) A is a row-major [M][K] matrix; a
     // chunk is 2^(kTc2RowBits - box_log2) boxes of 32 floats x 2^box_log2
     // consecutive rows; box j starts box_y[j] rows above the tile's base row,

@@ -223,7 +223,7 @@ __device__ __forceinline__ void tm_st32(uint32_t ta, const float* v) {
 struct Sm2 {
     // rawb: gather mode, all producers have stored their raw values of a stage
     uint64_t full[kRingGather], empty[kRingGather], rawb[kRingGather], rfull[kRaw], rempty[kRaw], tfull[2], tempty[2],
-        wready, drain, epi;
+        wready, drain, epi, never, pad_never;
     uint32_t tmem, pad;
     // staging offset (floats) of tile row r = rlo[r % 32] ^ rhi[r / 32]: the
     // row's base r * kCStride with its column swizzle folded in (linear in r)
@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         bar_init(&S->wready, kEpiT);
         bar_init(&S->drain, 1);
+        bar_init(&S->never, 1);
         bar_init(&S->epi, kEpiT);
     }
     if (tid < 32 + kRows / 32) {
@@ -509,6 +510,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(kRows >> 3) << 17) |
                                    (uint32_t(kM >> 4) << 24);
             bool ok = bar_wait(&S->wready, 0, t.err, 12, t.wait_ns);
+            // testing aid (xeb_plan_test_wait): a wait that runs out -- nothing
+            // arrives on `never` -- records a timeout, and every role then
+            // leaves its loop as after any failed wait
+            if (t.test_wait) ok = bar_wait(&S->never, 0, t.err, 30, t.wait_ns) && false;
             const bool four = t.split_terms == 4;
             fence_after();
             uint32_t it = 0, tc = 0;

@@ -158,12 +158,12 @@ def test_grid6x9m1_split_precision_matches_fp64_on_gpu():
     oracle reaches this size, so the TF32x3 result on a seeded slice of a
     sliced plan is checked against an FP64 recomputation on the GPU with the
     same tree, slices and slice (App. A, "Slicing": the partial sum over a
-    fixed set of slice values is a well-defined quantity).  200 bitstrings of
-    the 1,000,000-bitstring workload's generator."""
+    fixed set of slice values is a well-defined quantity).  The first 1,000
+    bitstrings of the 1,000,000-bitstring workload's generator."""
     import torch
     w = inputs.WORKLOADS["grid6x9m1_m14_k1000000"]
     circ = w.circuit()
-    bits = inputs.uniform_bitstrings(53, w.k, w.bitstring_seed)[:200]
+    bits = inputs.uniform_bitstrings(53, w.k, w.bitstring_seed)[:1000]
     o = B.xeb_default_opts()
     o.precision = B.XEB_PREC_TF32X3
     o.mem_budget = 16 << 30
