@@ -363,6 +363,7 @@ enum {
     XEB_KC_GEMM_STREAM = 10,  /* a4 memory-bound streaming contraction (SIMT)    */
     XEB_KC_GEMM_MEMO = 11,    /* a4 memo-trie levels: keys grouped by left key   */
     XEB_KC_GEMM_KDEEP = 12,   /* a4 keyed contractions with a deep summed index  */
+    XEB_KC_GEMM_TC_KDEEP = 13, /* a4 the same on tcgen05, split precision       */
     XEB_N_KC = 16
 };
 

@@ -40,6 +40,7 @@ namespace {
 int64_t align_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 constexpr int GK_TC2 = 101;  // tcgen05 split-precision kernel, W^T in tensor memory (tc_gemm2.cu)
+constexpr int GK_TCKD = 102; // tcgen05 split-precision kernel for deep-K keyed contractions (tc_kdeep.cu)
 // Defaults of the split-precision options (xeb_plan_opts.split_bits,
 // split_terms, timeout_ms): big parts of 10 bits on a common grid, four
 // products, 2 s per device-side wait.  With 11 bits the big*big sums of the
@@ -51,7 +52,7 @@ constexpr int kSplitTermsDefault = 4;
 constexpr uint32_t kTimeoutMsDefault = 2000;
 
 // kernel-form choices of a contraction (autotuner candidates)
-enum Choice { CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_SIMT = 3, CH_COUNT = 4 };
+enum Choice { CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_TCKD = 3, CH_SIMT = 4, CH_COUNT = 5 };
 
 struct GemmLaunch {
     CUtensorMap tmap;  // A of a TMA-mode tensor-core launch (64-byte aligned)
@@ -59,6 +60,7 @@ struct GemmLaunch {
     xebk::GemmDesc d;
     xebk::StreamDesc s;
     xebk::TcDesc tc;
+    xebk::KdDesc kd;
 };
 
 // Result bits below this C address bit are kept inside one tensor-core tile,
@@ -220,6 +222,46 @@ bool tc_grouped(const Analysis& an, const Op& op, const xebk::GemmDesc& d, xebk:
     t.n_groups = d.n_groups;
     t.c_key = d.c_key;
     t.gstart = d.gstart;
+    return true;
+}
+
+// Deep-K keyed tensor-core form (tc_kdeep.cu): C_u = A_uL(u) (M x K)
+// B_uR(u) (K x N), M, N in {16, 32}, K >= 64 a multiple of 64 complex: many
+// keys of a deep sum with small results.
+bool tc_kdeep(const Op& op, const xebk::GemmDesc& d, xebk::KdDesc& k) {
+    auto small = [](int64_t x) { return x == 16 || x == 32; };
+    if (op.kv < 2 || !d.uL || !d.uR || !small(op.M) || !small(op.N) || op.K < 64 || op.K % 64 != 0 || op.K > 8192)
+        return false;
+    if (d.nak != d.nbk || d.nak > xebk::kMaxLegs || d.nam > 5 || d.nbn > 5) return false;
+    std::memset(&k, 0, sizeof(k));
+    k.a_off = d.a_off;
+    k.a_key = d.a_key;
+    k.b_off = d.b_off;
+    k.b_key = d.b_key;
+    k.c_off = d.c_off;
+    k.c_key = d.c_key;
+    k.uL = d.uL;
+    k.uR = d.uR;
+    k.gstart = d.gstart;
+    k.n_groups = d.n_groups;
+    k.kv = op.kv;
+    k.M = int(op.M);
+    k.N = int(op.N);
+    k.K = int(op.K);
+    k.nak = d.nak;
+    k.nbk = d.nbk;
+    for (int i = 0; i < d.nam; ++i) {
+        k.apm[i] = d.apm[i];
+        k.cpm[i] = d.cpm[i];
+    }
+    for (int i = 0; i < d.nbn; ++i) {
+        k.bpn[i] = d.bpn[i];
+        k.cpn[i] = d.cpn[i];
+    }
+    for (int i = 0; i < d.nak; ++i) {
+        k.apk[i] = d.apk[i];
+        k.bpk[i] = d.bpk[i];
+    }
     return true;
 }
 
@@ -1361,6 +1403,16 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
         tc_common(false);
         return true;
     }
+    if (tf32 && (ch == CH_AUTO || ch == CH_TCKD) && tc_kdeep(op, d, g.kd)) {
+        g.kernel = GK_TCKD;
+        g.kd.err = reinterpret_cast<int32_t*>(tables + p->t_err);
+        g.kd.split_bits = p->opts.split_bits > 0 ? p->opts.split_bits : kSplitBitsDefault;
+        g.kd.split_terms = p->opts.split_terms > 0 ? p->opts.split_terms : kSplitTermsDefault;
+        g.kd.wait_ns = uint64_t(p->opts.timeout_ms > 0 ? p->opts.timeout_ms : kTimeoutMsDefault) * 1000000ull;
+        g.kd.test_wait = p->test_wait;
+        return true;
+    }
+    if (ch == CH_TCKD) return false;
     if (tc_ok && ch != CH_AUTO) return false;
     if (tf32 && (ch == CH_GROUPED || (ch == CH_AUTO && p->opts.reserved[4] == 1)) &&
         tc_grouped(p->an, op, d, g.tc)) {
@@ -1562,9 +1614,25 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 if (g.cpm[t2] < 0 || g.cpm[t2] >= rc || seen[g.cpm[t2]]++) { why = "result positions"; return false; }
             for (int t2 = 0; t2 < g.nbn; ++t2)
                 if (g.cpn[t2] < 0 || g.cpn[t2] >= rc || seen[g.cpn[t2]]++) { why = "result positions"; return false; }
-            if (!g.c_natural && p->gemms[i].kernel != GK_TC2) {
+            if (!g.c_natural && p->gemms[i].kernel != GK_TC2 && p->gemms[i].kernel != GK_TCKD) {
                 why = "non row-major result for a kernel that writes row-major only (node " +
                       std::to_string(op.node) + ")";
+                return false;
+            }
+        }
+        if (p->gemms[i].kernel == GK_TCKD) {
+            const xebk::KdDesc& k = p->gemms[i].kd;
+            bool bad = k.M != g.M || k.N != g.N || (k.M != 16 && k.M != 32) || (k.N != 16 && k.N != 32) ||
+                       k.K != g.K || k.K < 64 || k.K % 64 != 0 || k.K > 8192 || k.kv != g.kv || !k.uL || !k.uR ||
+                       k.a_off != g.a_off ||
+                       k.b_off != g.b_off || k.c_off != g.c_off || k.a_key != g.a_key || k.b_key != g.b_key ||
+                       k.c_key != g.c_key || k.nak != g.nak || k.nbk != g.nbk || !k.err || k.wait_ns == 0 ||
+                       k.split_bits < 8 || k.split_bits > 11 || (k.split_terms != 3 && k.split_terms != 4);
+            for (int t2 = 0; t2 < g.nam && !bad; ++t2) bad = k.apm[t2] != g.apm[t2] || k.cpm[t2] != g.cpm[t2];
+            for (int t2 = 0; t2 < g.nbn && !bad; ++t2) bad = k.bpn[t2] != g.bpn[t2] || k.cpn[t2] != g.cpn[t2];
+            for (int t2 = 0; t2 < g.nak && !bad; ++t2) bad = k.apk[t2] != g.apk[t2] || k.bpk[t2] != g.bpk[t2];
+            if (bad) {
+                why = "deep-K tensor-core form of node " + std::to_string(op.node);
                 return false;
             }
         }
@@ -1672,7 +1740,9 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
 template <typename T>
 cudaError_t launch_gemm_op(xeb_plan_s* p, const GemmLaunch& g, T* arena, char* tables, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
-    if (g.kernel == GK_TC2) {
+    if (g.kernel == GK_TCKD) {
+        if constexpr (sizeof(T) == 8) e = xebk::launch_tc_kdeep(g.kd, reinterpret_cast<float2*>(arena), p->n_sms, st);
+    } else if (g.kernel == GK_TC2) {
         if constexpr (sizeof(T) == 8) {
             if (g.tc.grp) e = xebk::launch_memo_prep<float2>(g.d, reinterpret_cast<float2*>(arena), tables + p->t_memo, st);
             if (e == cudaSuccess) e = xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st);
@@ -1726,7 +1796,8 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 static const int cls_of[7] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
                                               XEB_KC_GEMM_TAIL,    XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO,
                                               XEB_KC_GEMM_KDEEP};
-                ProfScope ps(p, st, g.kernel >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[g.kernel], fl, by, int(i));
+                ProfScope ps(p, st, g.kernel == GK_TCKD ? XEB_KC_GEMM_TC_KDEEP : g.kernel >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[g.kernel],
+                             fl, by, int(i));
                 XEB_CUDA(launch_gemm_op<T>(p, g, arena, tables, st));
             }
         }
@@ -2254,8 +2325,10 @@ extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t strea
 extern "C" xeb_status xeb_plan_test_wait(xeb_plan_s* p, int enable) {
     if (!p) return fail(XEB_EINVAL, "NULL plan");
     p->test_wait = enable != 0;
-    for (GemmLaunch& g : p->gemms)
+    for (GemmLaunch& g : p->gemms) {
         if (g.kernel == GK_TC2) g.tc.test_wait = p->test_wait;
+        if (g.kernel == GK_TCKD) g.kd.test_wait = p->test_wait;
+    }
     drop_graph(p, p->graph_plain);
     for (auto& g : p->graph_prof) drop_graph(p, g);
     return XEB_OK;
@@ -2347,7 +2420,7 @@ extern "C" xeb_status xeb_plan_profile_ops(xeb_plan_s* p, int cap, double* ms, d
             else if (!p->bound || p->gemms.size() <= size_t(i)) cls[i] = -1;
             else {
                 const int kk = p->gemms[size_t(i)].kernel;
-                cls[i] = kk >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[kk];
+                cls[i] = kk == GK_TCKD ? XEB_KC_GEMM_TC_KDEEP : kk >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[kk];
             }
         }
         if (shape) {

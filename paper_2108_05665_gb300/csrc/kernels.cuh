@@ -146,6 +146,26 @@ struct TcDesc {
     const int32_t* uL;
     const int32_t* uR;
 };
+// tcgen05 split-precision form of keyed contractions with a deep summed
+// index (tc_kdeep.cu): C_u = A_uL(u) (M x K) B_uR(u) (K x N) for every key u,
+// M, N in {16, 32}, K a multiple of 64 complex.  Operand
+// addressing as in GemmDesc (bit i of m / k / n at address bit apm / apk /
+// bpk / bpn [i] of the key's block; result bit i of m / n at cpm / cpn [i]).
+struct KdDesc {
+    int64_t a_off, a_key, b_off, b_key, c_off, c_key;
+    const int32_t* uL;
+    const int32_t* uR;
+    const int32_t* gstart;
+    int64_t n_groups, kv;
+    int M, N, K, nak, nbk;   // M, N in {16, 32}
+    int8_t apm[5], bpn[5], cpm[5], cpn[5];
+    int8_t apk[kMaxLegs], bpk[kMaxLegs];
+    int32_t* err;
+    int split_bits, split_terms, test_wait;
+    uint64_t wait_ns;
+};
+cudaError_t launch_tc_kdeep(const KdDesc& d, float2* arena, int n_sms, cudaStream_t st);
+
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 constexpr int kTc2RowBits = 7;               // tensor-memory variant: 128 state rows per tile
 
