@@ -583,3 +583,16 @@ def test_noalloc_xeb_refuses_bad_arguments_before_any_launch(lib):
     with pytest.raises(B.XebError) as e:
         B.xeb_linear_xeb_noalloc(misaligned, 10, 12, aligned, 0)
     assert "16-byte" in str(e.value)
+
+
+def test_deep_k_cases_hold_their_contraction_form():
+    """The plans of the deep-K tensor-core parity cases still contain the
+    keyed contraction each case is there to exercise."""
+    from kdeep_cases import CASES, plan_opts, deep_k_shapes
+    for case in CASES:
+        r, c = case["grid"]
+        circ = inputs.random_grid_circuit(r, c, case["cycles"], 4242)
+        bits = inputs.uniform_bitstrings(r * c, case["k"], 4343)
+        plan = B.Plan(circ, bits, opts=plan_opts(case))
+        assert case["shape"] in deep_k_shapes(plan), (case["id"], deep_k_shapes(plan))
+        plan.close()
