@@ -364,6 +364,7 @@ enum {
     XEB_KC_GEMM_MEMO = 11,    /* a4 memo-trie levels: keys grouped by left key   */
     XEB_KC_GEMM_KDEEP = 12,   /* a4 keyed contractions with a deep summed index  */
     XEB_KC_GEMM_TC_KDEEP = 13, /* a4 the same on tcgen05, split precision       */
+    XEB_KC_GEMM_KEYED = 14,   /* a4 keyed, few summed values, narrow results   */
     XEB_N_KC = 16
 };
 

@@ -417,7 +417,8 @@ def xeb_linear_xeb_noalloc(amps_dev_ptr: int, k: int, n_qubits: int, out_dev_ptr
 
 
 KERNEL_CLASSES = ["trie", "leaves", "permute", "gemm_tiled", "gemm_gemv", "gemm_tail", "gemm_generic",
-                  "accum", "xeb", "gemm_tc", "gemm_stream", "gemm_memo", "gemm_kdeep", "gemm_tc_kdeep"]
+                  "accum", "xeb", "gemm_tc", "gemm_stream", "gemm_memo", "gemm_kdeep", "gemm_tc_kdeep",
+                  "gemm_keyed"]
 XEB_N_KC = 16
 
 

@@ -52,7 +52,9 @@ constexpr int kSplitTermsDefault = 4;
 constexpr uint32_t kTimeoutMsDefault = 2000;
 
 // kernel-form choices of a contraction (autotuner candidates)
-enum Choice { CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_TCKD = 3, CH_SIMT = 4, CH_COUNT = 5 };
+enum Choice {
+    CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_TCKD = 3, CH_SIMT = 4, CH_KEYED = 5, CH_COUNT = 6
+};
 
 struct GemmLaunch {
     CUtensorMap tmap;  // A of a TMA-mode tensor-core launch (64-byte aligned)
@@ -61,6 +63,7 @@ struct GemmLaunch {
     xebk::StreamDesc s;
     xebk::TcDesc tc;
     xebk::KdDesc kd;
+    int64_t kvB = 1;   // GK_KEYED: distinct right operands (keys of B's node)
 };
 
 // Result bits below this C address bit are kept inside one tensor-core tile,
@@ -1277,9 +1280,13 @@ void layout_device(xeb_plan_s* p) {
     {   // memo-level contractions: per-group A offsets + packed B vectors (largest op)
         size_t mx = 16;
         for (const Op& op : p->prog.ops)
-            if (op.kind != OP_PERM && op.N == 1 && op.kv > 1)
-                mx = std::max(mx, xebk::memo_scratch_bytes(std::max(an.nodes[op.a_node].kv, an.nodes[op.b_node].kv),
-                                                           op.kv, op.K, p->elem));
+            if (op.kind != OP_PERM && op.kv > 1) {
+                if (op.N == 1)
+                    mx = std::max(mx, xebk::memo_scratch_bytes(std::max(an.nodes[op.a_node].kv, an.nodes[op.b_node].kv),
+                                                               op.kv, op.K, p->elem));
+                if (xebk::keyed_fits(op.M, op.N, op.K))
+                    mx = std::max(mx, xebk::keyed_scratch_bytes(an.nodes[op.b_node].kv, op.K, op.N));
+            }
         p->t_memo = take(int64_t(mx));
         p->memo_bytes = mx;
     }
@@ -1364,6 +1371,18 @@ std::vector<char> fold_host_data(xeb_plan_s* p) {
     return h;
 }
 
+// Keyed SIMT form (keyed.cu): complex64, k_v > 1 keys grouped by left key (or
+// one group), K in {4, 8, 16, 32}, N in {1, 2, 4, 8, 16}, M a multiple of 32,
+// row-major results at even float2 offsets, summed bits below address bit 31.
+bool keyed_ok(const xeb_plan_s* p, const Op& op, const xebk::GemmDesc& d) {
+    if (p->elem != 8 || op.kv <= 1 || !xebk::keyed_fits(op.M, op.N, op.K) || !d.c_natural) return false;
+    if (!d.gstart && d.n_groups != 1) return false;
+    if (d.c_off % 2 != 0 || d.c_key % 2 != 0) return false;
+    for (int i = 0; i < d.nak; ++i)
+        if (d.apk[i] > 30) return false;
+    return xebk::keyed_scratch_bytes(p->an.nodes[op.b_node].kv, op.K, op.N) <= p->memo_bytes;
+}
+
 // Kernel form of one contraction: CH_AUTO follows the options; the others
 // force a form (the autotuner's candidates).  False if the form does not fit.
 bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
@@ -1421,6 +1440,13 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
         g.tc.grp_a = reinterpret_cast<const int64_t*>(tables + p->t_memo);
         g.tc.bpack_off = (p->off_tables + p->t_memo + ((d.n_groups * 8 + 255) & ~int64_t(255))) / 8;
         g.s = xebk::StreamDesc{};
+        return true;
+    }
+    // keyed contractions with few summed values and narrow results, complex64
+    // (keyed.cu): the default SIMT form where it fits
+    if ((ch == CH_AUTO || ch == CH_KEYED) && keyed_ok(p, op, d)) {
+        g.kernel = xebk::GK_KEYED;
+        g.kvB = p->an.nodes[op.b_node].kv;
         return true;
     }
     if (ch != CH_AUTO && ch != CH_SIMT) return false;
@@ -1710,6 +1736,13 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
                 }
             }
         }
+        if (p->gemms[i].kernel == xebk::GK_KEYED) {
+            const GemmLaunch& gl = p->gemms[i];
+            if (!keyed_ok(p, op, g) || gl.kvB != kb || (kb > 1 && !g.uR)) {
+                why = "keyed form of node " + std::to_string(op.node);
+                return false;
+            }
+        }
         if (p->gemms[i].kernel == xebk::GK_MEMO &&
             xebk::memo_scratch_bytes(p->gemms[i].d.n_groups, g.kv, g.K, p->elem) > p->memo_bytes) {
             why = "memo-level scratch of node " + std::to_string(op.node);
@@ -1747,6 +1780,11 @@ cudaError_t launch_gemm_op(xeb_plan_s* p, const GemmLaunch& g, T* arena, char* t
             if (g.tc.grp) e = xebk::launch_memo_prep<float2>(g.d, reinterpret_cast<float2*>(arena), tables + p->t_memo, st);
             if (e == cudaSuccess) e = xebk::launch_tc_gemm2(g.tc, g.tmap, reinterpret_cast<float2*>(arena), p->n_sms, st);
         }
+    } else if (g.kernel == xebk::GK_KEYED) {
+        if constexpr (sizeof(T) == 8)
+            e = xebk::launch_gemm_keyed(g.d, g.kvB, reinterpret_cast<float2*>(arena), tables + p->t_memo, p->n_sms, st);
+        else
+            e = cudaErrorInvalidValue;
     } else if (g.kernel == xebk::GK_MEMO) {
         e = xebk::launch_gemm_memo<T>(g.d, g.s, arena, tables + p->t_memo, st);
     } else if (g.kernel == xebk::GK_STREAM) {
@@ -1793,9 +1831,9 @@ xeb_status run_slices(xeb_plan_s* p, double2* amps_out, cudaStream_t st) {
                 const double fl = 8.0 * double(op.kv) * double(op.M) * double(op.N) * double(op.K);
                 const double by = es * (ka * double(op.M) * double(op.K) + kb * double(op.K) * double(op.N) +
                                         double(op.kv) * double(op.M) * double(op.N));
-                static const int cls_of[7] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
+                static const int cls_of[8] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV,
                                               XEB_KC_GEMM_TAIL,    XEB_KC_GEMM_STREAM, XEB_KC_GEMM_MEMO,
-                                              XEB_KC_GEMM_KDEEP};
+                                              XEB_KC_GEMM_KDEEP,   XEB_KC_GEMM_KEYED};
                 ProfScope ps(p, st, g.kernel == GK_TCKD ? XEB_KC_GEMM_TC_KDEEP : g.kernel >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[g.kernel],
                              fl, by, int(i));
                 XEB_CUDA(launch_gemm_op<T>(p, g, arena, tables, st));
@@ -2407,8 +2445,8 @@ extern "C" xeb_status xeb_plan_profile_ops(xeb_plan_s* p, int cap, double* ms, d
     if (!p || !n_ops) return fail(XEB_EINVAL, "NULL plan or n_ops");
     drain_profile(p);
     const Program& pr = p->prog;
-    static const int cls_of[7] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV, XEB_KC_GEMM_TAIL,
-                                  XEB_KC_GEMM_STREAM,  XEB_KC_GEMM_MEMO,  XEB_KC_GEMM_KDEEP};
+    static const int cls_of[8] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV, XEB_KC_GEMM_TAIL,
+                                  XEB_KC_GEMM_STREAM,  XEB_KC_GEMM_MEMO,  XEB_KC_GEMM_KDEEP, XEB_KC_GEMM_KEYED};
     const int n = int(pr.ops.size());
     *n_ops = n;
     for (int i = 0; i < std::min(n, cap); ++i) {

@@ -80,7 +80,8 @@ struct StreamDesc {
     int8_t pos[32];
 };
 
-enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4, GK_MEMO = 5, GK_KDEEP = 6 };
+enum GemmKernel { GK_GENERIC = 0, GK_TILED = 1, GK_GEMV = 2, GK_TAIL = 3, GK_STREAM = 4, GK_MEMO = 5, GK_KDEEP = 6,
+                  GK_KEYED = 7 };
 constexpr int kKdTile = 32;   // deep-K contractions: 32 x 32 result tile per CTA
 constexpr int kKdChunk = 64;  // summed-index chunk staged per step (8 per warp)
 constexpr int kStreamMaxK = 64, kStreamMaxN = 64;
@@ -165,6 +166,14 @@ struct KdDesc {
     uint64_t wait_ns;
 };
 cudaError_t launch_tc_kdeep(const KdDesc& d, float2* arena, int n_sms, cudaStream_t st);
+// Keyed contractions with K in {4, 8, 16, 32}, N in {1, 2, 4, 8, 16} complex,
+// M >= 32 a multiple of 32, row-major results, keys grouped by left key
+// (keyed.cu, complex64).  Scratch: keyed_scratch_bytes(kvB, K, N) bytes,
+// 256-byte aligned, for the packed copy of the kvB right operands.
+bool keyed_fits(int64_t M, int64_t N, int64_t K);
+size_t keyed_scratch_bytes(int64_t kvB, int64_t K, int64_t N);
+cudaError_t launch_gemm_keyed(const GemmDesc& g, int64_t kvB, float2* arena, char* scratch, int n_sms,
+                              cudaStream_t st);
 
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 constexpr int kTc2RowBits = 7;               // tensor-memory variant: 128 state rows per tile

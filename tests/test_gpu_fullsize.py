@@ -29,6 +29,8 @@ def test_grid5x6_all_amplitudes(fixture, precision):
     amps, F, plan = run(circ, bits, precision=precision)
     if precision == B.XEB_PREC_TF32X3:
         assert "gemm_tc" in plan.profile, plan.profile
+    # the memo-trie levels (keyed, N = 1, K = 16) run on the keyed SIMT kernel
+    assert plan.profile.get("gemm_keyed", {}).get("launches", 0) > 0, plan.profile
     err = rel_err(amps, ref, circ.n_qubits)
     shrink = -np.mean(np.real(np.conj(ref) * (amps - ref))) / np.mean(np.abs(ref) ** 2)
     print("max rel err %.3e  median %.3e  mean shrink %.2e  |dF| %.3e"
