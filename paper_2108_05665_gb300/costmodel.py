@@ -17,12 +17,19 @@ from . import binding as B
 N_FEATURES = B.XEB_N_FEATURES
 
 
-def time_plan(circ, bits, tree, slices, opts, reps=3, warmup=1):
+def time_plan(circ, bits, tree, slices, opts, reps=3, warmup=1, slice_count=None, slice_seed=12345):
     """Measured milliseconds of one step (key tables + contraction + XEB) of
-    the plan with this tree and slice set, bitstrings already on the device."""
+    the plan with this tree and slice set, bitstrings already on the device.
+    slice_count: run only that many slices (a seeded subset,
+    xeb_set_slice_subset) and scale the time to the full sum over slices."""
     import torch
     plan = B.Plan(circ, bits, tree=tree, slices=slices or None, opts=opts).bind()
     try:
+        scale = 1.0
+        if slice_count:
+            n_slices = plan.stats()["n_slices"]
+            n_run = B.xeb_set_slice_subset(plan.handle, min(1.0, slice_count / n_slices), slice_seed)
+            scale = n_slices / n_run
         stream = torch.cuda.current_stream()
         sp = stream.cuda_stream
         dev = torch.from_numpy(np.asarray(bits, dtype=np.uint64).view(np.int64).copy()).cuda()
@@ -42,7 +49,7 @@ def time_plan(circ, bits, tree, slices, opts, reps=3, warmup=1):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1) / reps * scale
     finally:
         plan.close()
 
@@ -98,9 +105,9 @@ class CostModel:
         self.mlp.forward(Xd.data_ptr(), len(X), yd.data_ptr(), sp)
         return yd.cpu().numpy().astype(np.float64)
 
-    def save(self, path):
+    def save(self, path, n_train=0):
         np.savez(path, weights=self.mlp.get_weights(), mean=self.mean, scale=self.scale,
-                 n_hidden=self.n_hidden, n_layers=self.n_layers)
+                 n_hidden=self.n_hidden, n_layers=self.n_layers, n_train=n_train)
 
     @classmethod
     def load(cls, path, seed=0):
@@ -127,7 +134,7 @@ def choose(circ, bits, opts=None, model=None, max_cands=256):
     return c
 
 
-def choose_verified(circ, bits, opts=None, model=None, top=3, max_cands=256, reps=3):
+def choose_verified(circ, bits, opts=None, model=None, top=3, max_cands=256, reps=3, slice_count=None):
     """The model proposes its `top` fastest-predicted candidates; they and the
     plain planner's plan are timed on the GPU and the fastest measured one is
     kept (so the result is never a plan the plain planner beats by more than
@@ -138,7 +145,7 @@ def choose_verified(circ, bits, opts=None, model=None, top=3, max_cands=256, rep
     tree, slices = plain.tree()
     plain.close()
     best = {"tree": tree, "slices": slices, "source": "plain",
-            "measured_ms": time_plan(circ, bits, tree, slices, o, reps=reps)}
+            "measured_ms": time_plan(circ, bits, tree, slices, o, reps=reps, slice_count=slice_count)}
     if model is None:
         return best
     cands = B.xeb_plan_candidates(circ, bits, o, max_cands)
@@ -148,7 +155,7 @@ def choose_verified(circ, bits, opts=None, model=None, top=3, max_cands=256, rep
     for i in np.argsort(pred)[:top]:
         c = cands[int(i)]
         try:
-            ms = time_plan(circ, bits, c["tree"], c["slices"], o, reps=reps)
+            ms = time_plan(circ, bits, c["tree"], c["slices"], o, reps=reps, slice_count=slice_count)
         except B.XebError:
             continue
         if ms < best["measured_ms"]:

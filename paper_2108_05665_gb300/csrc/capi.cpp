@@ -53,7 +53,8 @@ constexpr uint32_t kTimeoutMsDefault = 2000;
 
 // kernel-form choices of a contraction (autotuner candidates)
 enum Choice {
-    CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_TCKD = 3, CH_SIMT = 4, CH_KEYED = 5, CH_COUNT = 6
+    CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_TCKD = 3, CH_SIMT = 4, CH_KEYED = 5, CH_KEYED2 = 6,
+    CH_COUNT = 7
 };
 
 struct GemmLaunch {
@@ -64,6 +65,7 @@ struct GemmLaunch {
     xebk::TcDesc tc;
     xebk::KdDesc kd;
     int64_t kvB = 1;   // GK_KEYED: distinct right operands (keys of B's node)
+    int rpt = 1;       // GK_KEYED: rows per lane (1 or 2)
 };
 
 // Result bits below this C address bit are kept inside one tensor-core tile,
@@ -1383,6 +1385,11 @@ bool keyed_ok(const xeb_plan_s* p, const Op& op, const xebk::GemmDesc& d) {
     return xebk::keyed_scratch_bytes(p->an.nodes[op.b_node].kv, op.K, op.N) <= p->memo_bytes;
 }
 
+// Rows per lane of the keyed form when the autotuner has not chosen: two
+// wherever they fit (each uniform load of B then feeds twice the
+// multiply-adds).
+bool keyed_rows2_default(const Op& op) { return op.K <= 16; }
+
 // Kernel form of one contraction: CH_AUTO follows the options; the others
 // force a form (the autotuner's candidates).  False if the form does not fit.
 bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
@@ -1444,11 +1451,15 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
     }
     // keyed contractions with few summed values and narrow results, complex64
     // (keyed.cu): the default SIMT form where it fits
-    if ((ch == CH_AUTO || ch == CH_KEYED) && keyed_ok(p, op, d)) {
+    if ((ch == CH_AUTO || ch == CH_KEYED || ch == CH_KEYED2) && keyed_ok(p, op, d)) {
+        const bool rows2 = xebk::keyed_fits_rows2(op.M, op.N, op.K);
+        if (ch == CH_KEYED2 && !rows2) return false;
         g.kernel = xebk::GK_KEYED;
         g.kvB = p->an.nodes[op.b_node].kv;
+        g.rpt = ch == CH_KEYED2 || (ch == CH_AUTO && rows2 && keyed_rows2_default(op)) ? 2 : 1;
         return true;
     }
+    if (ch == CH_KEYED || ch == CH_KEYED2) return false;
     if (ch != CH_AUTO && ch != CH_SIMT) return false;
     if (stream_tile(op, p->elem, g.s))
         g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
@@ -1738,7 +1749,8 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
         }
         if (p->gemms[i].kernel == xebk::GK_KEYED) {
             const GemmLaunch& gl = p->gemms[i];
-            if (!keyed_ok(p, op, g) || gl.kvB != kb || (kb > 1 && !g.uR)) {
+            if (!keyed_ok(p, op, g) || gl.kvB != kb || (kb > 1 && !g.uR) ||
+                !(gl.rpt == 1 || (gl.rpt == 2 && xebk::keyed_fits_rows2(g.M, g.N, g.K)))) {
                 why = "keyed form of node " + std::to_string(op.node);
                 return false;
             }
@@ -1782,7 +1794,7 @@ cudaError_t launch_gemm_op(xeb_plan_s* p, const GemmLaunch& g, T* arena, char* t
         }
     } else if (g.kernel == xebk::GK_KEYED) {
         if constexpr (sizeof(T) == 8)
-            e = xebk::launch_gemm_keyed(g.d, g.kvB, reinterpret_cast<float2*>(arena), tables + p->t_memo, p->n_sms, st);
+            e = xebk::launch_gemm_keyed(g.d, g.kvB, g.rpt, reinterpret_cast<float2*>(arena), tables + p->t_memo, p->n_sms, st);
         else
             e = cudaErrorInvalidValue;
     } else if (g.kernel == xebk::GK_MEMO) {
@@ -2322,7 +2334,9 @@ extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t strea
         for (int ch = 0; ch < CH_COUNT && s == XEB_OK; ++ch) {
             GemmLaunch g = keep;
             if (!select_kernel(p, pr.ops[i], ch, g)) continue;
-            const std::pair<int, int> form{g.kernel, g.kernel == GK_TC2 ? g.tc.tma + 2 * g.tc.grp : 0};
+            const std::pair<int, int> form{g.kernel, g.kernel == GK_TC2      ? g.tc.tma + 2 * g.tc.grp
+                                                     : g.kernel == xebk::GK_KEYED ? g.rpt
+                                                                                  : 0};
             if (std::find(seen.begin(), seen.end(), form) != seen.end()) continue;
             seen.push_back(form);
             p->gemms[i] = g;
@@ -2346,7 +2360,8 @@ extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t strea
         const auto best = *std::min_element(timed.begin(), timed.end());
         GemmLaunch g = keep;
         select_kernel(p, pr.ops[i], best.second, g);
-        const bool differs = g.kernel != keep.kernel || (g.kernel == GK_TC2 && (g.tc.tma != keep.tc.tma || g.tc.grp != keep.tc.grp));
+        const bool differs = g.kernel != keep.kernel || (g.kernel == GK_TC2 && (g.tc.tma != keep.tc.tma || g.tc.grp != keep.tc.grp)) ||
+                             (g.kernel == xebk::GK_KEYED && g.rpt != keep.rpt);
         p->choice[i] = best.second;
         p->gemms[i] = g;
         changed += differs;

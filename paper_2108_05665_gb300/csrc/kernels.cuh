@@ -170,10 +170,14 @@ cudaError_t launch_tc_kdeep(const KdDesc& d, float2* arena, int n_sms, cudaStrea
 // M >= 32 a multiple of 32, row-major results, keys grouped by left key
 // (keyed.cu, complex64).  Scratch: keyed_scratch_bytes(kvB, K, N) bytes,
 // 256-byte aligned, for the packed copy of the kvB right operands.
+// rows_per_lane = 2: each lane takes two rows 32 apart (items of 64 rows,
+// M % 64 == 0, K <= 16), so each uniform load of B feeds twice the
+// multiply-adds.
 bool keyed_fits(int64_t M, int64_t N, int64_t K);
+bool keyed_fits_rows2(int64_t M, int64_t N, int64_t K);
 size_t keyed_scratch_bytes(int64_t kvB, int64_t K, int64_t N);
-cudaError_t launch_gemm_keyed(const GemmDesc& g, int64_t kvB, float2* arena, char* scratch, int n_sms,
-                              cudaStream_t st);
+cudaError_t launch_gemm_keyed(const GemmDesc& g, int64_t kvB, int rows_per_lane, float2* arena, char* scratch,
+                              int n_sms, cudaStream_t st);
 
 constexpr int32_t kErrTimeout = 0x40000000;  // | role code
 constexpr int kTc2RowBits = 7;               // tensor-memory variant: 128 state rows per tile

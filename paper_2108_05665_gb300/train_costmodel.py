@@ -84,6 +84,39 @@ def evaluate(model, args):
     return evals
 
 
+def evaluate_workload(model, name, slice_count, reps, max_cands):
+    """A benchmark workload (e.g. the 53-qubit sliced one): every candidate,
+    the plain planner's plan, the model's choice and the verified choice,
+    each timed on the same seeded subset of slice_count slices and scaled to
+    the full sum over slices."""
+    w = inputs.WORKLOADS[name]
+    circ = w.circuit()
+    bits = inputs.uniform_bitstrings(w.n_qubits, w.k, w.bitstring_seed)
+    o = B.xeb_default_opts()
+    o.precision = B.XEB_PREC_TF32X3
+    t0 = time.time()
+    plain = B.Plan(circ, bits, opts=o)
+    plain_tree, plain_slices = plain.tree()
+    plain.close()
+    t_plan = time.time() - t0
+    cands = B.xeb_plan_candidates(circ, bits, o, max_cands)
+    ms = []
+    for c in cands:
+        try:
+            ms.append(time_plan(circ, bits, c["tree"], c["slices"], o, reps=reps, slice_count=slice_count))
+        except B.XebError:
+            ms.append(float("nan"))
+    ms = np.array(ms)
+    pred = model.predict(np.array([c["features"] for c in cands])) if cands else np.array([])
+    t_plain = time_plan(circ, bits, plain_tree, plain_slices, o, reps=reps, slice_count=slice_count)
+    pick = int(np.argmin(pred)) if len(pred) else -1
+    ver = choose_verified(circ, bits, o, model, top=3, max_cands=max_cands, reps=reps, slice_count=slice_count)
+    return {"workload": name, "slice_count": slice_count, "plain_plan_seconds": t_plan, "n_cands": len(cands),
+            "cand_ms": [float(x) for x in ms], "pred_log2_ms": [float(x) for x in pred], "plain_ms": t_plain,
+            "model_ms": float(ms[pick]) if pick >= 0 else None, "verified_ms": ver["measured_ms"],
+            "verified_source": ver["source"], "best_ms": float(np.nanmin(ms)) if len(ms) else None}
+
+
 def geo_means(evals):
     def gm(a, b):
         return float(np.exp(np.mean([np.log(e[a] / e[b]) for e in evals]))) if evals else None
@@ -106,6 +139,12 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--seed", type=int, default=5000)
     ap.add_argument("--eval-only", default=None, help="saved weights: skip data generation and training")
+    ap.add_argument("--eval-workload", action="append", default=[],
+                    help="also compare on this benchmark workload (inputs.WORKLOADS), sliced plans timed on a subset")
+    ap.add_argument("--eval-slice-count", type=int, default=4)
+    ap.add_argument("--max-samples", type=int, default=0, help="stop generating data after this many timed plans")
+    ap.add_argument("--data-out", default=None, help="save the generated (features, log2 ms) pairs here")
+    ap.add_argument("--data-in", default=None, help="train on saved pairs instead of generating them")
     args = ap.parse_args(argv)
     build.build()
     B.load()
@@ -113,32 +152,45 @@ def main(argv=None):
         model = CostModel.load(args.eval_only)
         summary = {"weights": args.eval_only, "eval": evaluate(model, args)}
         summary.update(geo_means(summary["eval"]))
+        summary["workloads"] = [evaluate_workload(model, n, args.eval_slice_count, args.reps, args.max_cands)
+                                for n in args.eval_workload]
         with open(args.summary, "w") as fh:
             json.dump(summary, fh, indent=1)
         print(json.dumps({k: v for k, v in summary.items() if k != "eval"}))
         return
     t0 = time.time()
-    X, y, n_circ = [], [], 0
-    for i in range(args.train_circuits):
-        if time.time() - t0 > args.max_seconds:
-            break
-        _, f, ms = measure_circuit(circuit_spec(i, args.seed), args.max_cands, args.reps)
-        if len(ms):
-            X.append(f)
-            y.append(np.log2(ms))
-            n_circ += 1
-    X = np.concatenate(X)
-    y = np.concatenate(y)
-    t_data = time.time() - t0
+    if args.data_in:
+        d = np.load(args.data_in)
+        X, y, n_circ, t_data = d["X"], d["y"], int(d["n_circuits"]), float(d["seconds"])
+    else:
+        X, y, n_circ = [], [], 0
+        for i in range(args.train_circuits):
+            if time.time() - t0 > args.max_seconds or (args.max_samples and sum(len(v) for v in y) >= args.max_samples):
+                break
+            _, f, ms = measure_circuit(circuit_spec(i, args.seed), args.max_cands, args.reps)
+            if len(ms):
+                X.append(f)
+                y.append(np.log2(ms))
+                n_circ += 1
+        X = np.concatenate(X)
+        y = np.concatenate(y)
+        t_data = time.time() - t0
+        if args.data_out:
+            np.savez(args.data_out, X=X, y=y, n_circuits=n_circ, seconds=t_data)
     model = CostModel(seed=1)
     hist = model.fit(X, y, epochs=args.epochs, batch=256, lr=1e-3)
-    model.save(args.out)
+    model.save(args.out, n_train=int(len(y)))
     pred = model.predict(X)
     train_rmse = float(np.sqrt(np.mean((pred - y) ** 2)))
-    evals = evaluate(model, args)
     summary = {"train_circuits": n_circ, "train_samples": int(len(y)), "data_seconds": t_data,
-               "epochs": args.epochs, "final_loss": hist[-1], "train_rmse_log2": train_rmse, "eval": evals}
+               "epochs": args.epochs, "final_loss": hist[-1], "train_rmse_log2": train_rmse}
+    with open(args.summary, "w") as fh:   # written before the (long) evaluation
+        json.dump(summary, fh, indent=1)
+    evals = evaluate(model, args)
+    summary["eval"] = evals
     summary.update(geo_means(evals))
+    summary["workloads"] = [evaluate_workload(model, n, args.eval_slice_count, args.reps, args.max_cands)
+                            for n in args.eval_workload]
     with open(args.summary, "w") as fh:
         json.dump(summary, fh, indent=1)
     print(json.dumps({k: v for k, v in summary.items() if k != "eval"}))
