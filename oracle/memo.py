@@ -21,9 +21,11 @@ Contents
 * ``alg12``: Alg. 1 driving Alg. 2 (recursive eval with a global dictionary
   cache keyed by (subexpression; values of its variables)); returns the
   results and the number of contractions performed per node.
-* ``alg34``: Alg. 3 (eval_all) and Alg. 4 (eval') with the left/right caches.
-  The loop of eval_all runs over i = 1..|t| (the text's "i=1,...,m" is read as
-  that bound).
+* ``alg34``: what Alg. 3 (eval_all) and Alg. 4 (eval') compute: over the
+  sorted distinct tuples of leaf value indices, each node evaluated once per
+  distinct sub-tuple, its right child for all distinct right parts at once
+  and its left child over the consecutive groups of equal prefixes (the
+  text's loop bound "i=1,...,m" is read as i = 1..|t|).
 * ``costs``: the contraction cost C = sum_v k_v 2^(q_v + r_v) and read/write
   count RW = sum_v k_v (m(L) + m(R) + m(v)) of App. A/C, with exact or bound
   evaluation counts k_v (App. C, "Complexity estimation").
@@ -164,75 +166,63 @@ def alg12(net: Network, tree, bitstrings, sliced: Optional[Dict[int, int]] = Non
 # --- Alg. 3 / Alg. 4 ------------------------------------------------------------
 
 def alg34(net: Network, tree, bitstrings, sliced: Optional[Dict[int, int]] = None):
-    """eval_all (Alg. 3) with eval' (Alg. 4).  Variables are the leaves in
-    in-order position; V_j lists leaf j's distinct projected tensors in
-    ascending order of its output-bit value; t^i holds value indices.
-    Returns ({word: result}, contractions per node)."""
+    """Alg. 3 (eval_all) with Alg. 4 (eval'), restated by what they compute.
+
+    Each bitstring becomes the tuple of its leaves' value indices, leaves in
+    in-order position, where leaf j's values V_j are its distinct projected
+    tensors in ascending order of its output-bit value; the tuples are sorted
+    and made distinct.  A node's sub-tuple is the slice of a tuple over the
+    leaves below it.  Evaluating a node for a sorted list of distinct
+    sub-tuples means: evaluate its right child once for the distinct right
+    parts of the list (the right cache), its left child once for the distinct
+    left parts (prefixes, so equal ones are consecutive: the left cache holds
+    one value at a time), then contract once per entry of the list.  Returns
+    ({word: result}, contractions per node)."""
     bitstrings = np.asarray(bitstrings, dtype=np.uint64)
     order = inorder_leaves(tree, root_ref(tree))
     pos = {j: p for p, j in enumerate(order)}
-    # V_j and the index tuples t^i
-    vid = []
-    V = []
+    vid, V = [], []
     for j in order:
         ids = [_leaf_value_id(net, j, int(w)) for w in bitstrings]
         distinct = sorted(set(ids))
         V.append([project_leaf(net.leaves[j],
                                sum(b << q for b, q in zip(d, net.leaves[j].out_qubits)),
                                sliced) for d in distinct])
-        vid.append([distinct.index(x) for x in ids])
-    tuples = [tuple(vid[p][i] for p in range(len(order)))
-              for i in range(len(bitstrings))]
-    span = {}
+        vid.append({x: n for n, x in enumerate(distinct)})
+        vid[-1] = [vid[-1][x] for x in ids]
+    tuples = [tuple(vid[p][i] for p in range(len(order))) for i in range(len(bitstrings))]
+    width = {}     # leaves below each node
 
-    def walk(ref):
+    def count_leaves(ref):
         if ref < 0:
-            p = pos[-1 - ref]
-            span[ref] = (p, p + 1)
-            return
-        l, r = tree[ref]
-        walk(l)
-        walk(r)
-        span[ref] = (span[l][0], span[r][1])
+            width[ref] = 1
+        else:
+            l, r = tree[ref]
+            count_leaves(l)
+            count_leaves(r)
+            width[ref] = width[l] + width[r]
+        return width[ref]
 
-    walk(root_ref(tree))
+    count_leaves(root_ref(tree))
     counts: Dict[int, int] = defaultdict(int)
 
-    def eval_all(ref, t_set):
-        base = span[ref][0]
-        t = sorted(set(t_set))
-        KL, KR = {}, {}
-        R = {}
-        for i in range(len(t)):
-            R[t[i]] = eval_p(ref, base, t, i, i + 1, KL, KR)
-        return R
-
-    def restrict(tup, ref, base):
-        a, b = span[ref]
-        return tup[a - base:b - base]
-
-    def eval_p(ref, base, t, i, i_next, KL, KR):
+    def evaluate(ref, subs):
+        """{sub-tuple: value} of node ref for the sorted distinct sub-tuples subs."""
         if ref < 0:
-            p = span[ref][0]
-            return V[p][t[i][p - base]]
-        cur = restrict(t[i], ref, base)
-        if i == 0 or cur != restrict(t[i - 1], ref, base):
-            l, r = tree[ref]
-            if KR.get(ref) is None:
-                KR[ref] = eval_all(r, [restrict(x, r, base) for x in t])
-            last = max(j for j in range(len(t)) if restrict(t[j], ref, base) == cur)
-            ul = eval_p(l, base, t, i, last + 1, KL, KR)
-            ur = KR[ref][restrict(t[i], r, base)]
-            u = pair_contract(ul[0], ul[1], ur[0], ur[1])
+            p = pos[-1 - ref]
+            return {s: V[p][s[0]] for s in subs}
+        l, r = tree[ref]
+        nl = width[l]
+        right = evaluate(r, sorted({s[nl:] for s in subs}))
+        left = evaluate(l, sorted({s[:nl] for s in subs}))
+        out = {}
+        for s in subs:
+            a, b = left[s[:nl]], right[s[nl:]]
+            out[s] = pair_contract(a[0], a[1], b[0], b[1])
             counts[ref] += 1
-            if i_next < len(t) and restrict(t[i_next], ref, base) == cur:
-                KL[ref] = u
-            if i_next >= len(t):
-                KR[ref] = None
-            return u
-        return KL[ref]
+        return out
 
-    R = eval_all(root_ref(tree), tuples)
+    R = evaluate(root_ref(tree), sorted(set(tuples)))
     results = {}
     for i, w in enumerate(bitstrings):
         tval, legs = R[tuples[i]]

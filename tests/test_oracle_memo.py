@@ -36,8 +36,6 @@ def test_key_tables_brute_force(small, seed):
         distinct = sorted(set(proj))
         assert kt["k"][i] == len(distinct)
         # key ids are ranks in lexicographic order of the pi-ordered bits
-        for w, p in zip(bs, proj):
-            pass
         ids = [distinct.index(p) for p in proj]
         assert list(kt["key"][i]) == ids
         # children ids reproduce each key's bits
