@@ -96,36 +96,62 @@ def test_training_fits_a_known_function():
     m.close()
 
 
-def test_learned_planner_choice_on_held_out_circuit():
-    """The trained model (committed weights) proposes plans for a circuit it
-    was not trained on; the verified choice is timed against the plain
-    planner's plan and its amplitudes still match the oracle."""
+# Held-out circuits of the training script's family (train_costmodel.circuit_spec
+# with its default base seed; training draws indices 0, 1, ... below its
+# circuit count, evaluation starts at 10,000): 4x4 grid, 8 and 10 cycles, 300 bitstrings, TF32x3; 3x6
+# grid, 12 cycles, 300 bitstrings, FP32.
+HELD_OUT = (10000, 10003, 10006)
+# The verified choice keeps the plain plan when the model proposes nothing
+# faster, so a model that gains nothing gives a ratio of 1 up to timing noise
+# (a few percent at these step times); the bound asks for a real gain.
+GAIN_BOUND = 0.90
+
+
+def _median_ms(circ, bits, tree, slices, o, rounds=5, reps=5):
+    from paper_2108_05665_gb300 import costmodel
+    return float(np.median([costmodel.time_plan(circ, bits, tree, slices, o, reps=reps) for _ in range(rounds)]))
+
+
+def test_learned_planner_gains_on_held_out_circuits():
+    """The trained model (committed weights) proposes plans for circuits it
+    was not trained on; the verified choice (the model's three
+    fastest-predicted plans and the plain planner's plan, the fastest measured
+    kept) is timed again against the plain planner's plan, alternating the two,
+    and the geometric mean of the time ratios must show a gain.  The chosen
+    plans' amplitudes still match the oracle."""
     import os
-    from paper_2108_05665_gb300 import costmodel, inputs
+    import torch
+    from paper_2108_05665_gb300 import costmodel, train_costmodel
     from oracle import statevec
     from gpu_util import rel_err
     w = os.path.join(os.path.dirname(costmodel.__file__), "costmodel_weights.npz")
     model = costmodel.CostModel.load(w)
-    circ = inputs.random_grid_circuit(4, 4, 10, 424242)
-    bits = inputs.uniform_bitstrings(16, 300, 434343)
-    o = B.xeb_default_opts()
-    o.precision = B.XEB_PREC_TF32X3
-    cands = B.xeb_plan_candidates(circ, bits, o)
-    pred = model.predict(np.array([c["features"] for c in cands]))
-    assert np.all(np.isfinite(pred))
-    ch = costmodel.choose_verified(circ, bits, o, model, top=3)
-    plain = B.Plan(circ, bits, opts=o)
-    tree, slices = plain.tree()
-    plain.close()
-    t_plain = costmodel.time_plan(circ, bits, tree, slices, o)
-    print("plain %.3f ms, verified %.3f ms (%s)" % (t_plain, ch["measured_ms"], ch["source"]))
-    assert ch["measured_ms"] <= 1.10 * t_plain
-    plan = B.Plan(circ, bits, tree=ch["tree"], slices=ch["slices"] or None, opts=o).bind()
-    import torch
-    st = torch.cuda.current_stream().cuda_stream
-    hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
-    ha = torch.empty(2 * len(bits), dtype=torch.float64).pin_memory()
-    B.xeb_run(plan.handle, hb.data_ptr(), len(bits), ha.data_ptr(), st)
-    amps = ha.numpy().view(np.complex128)
-    assert rel_err(amps, statevec.amplitudes(circ, bits), 16).max() < 1e-5
-    plan.close()
+    ratios = []
+    for idx in HELD_OUT:
+        spec = train_costmodel.circuit_spec(idx, 5000)
+        circ, bits, o = train_costmodel.make(spec)
+        cands = B.xeb_plan_candidates(circ, bits, o)
+        assert np.all(np.isfinite(model.predict(np.array([c["features"] for c in cands]))))
+        ch = costmodel.choose_verified(circ, bits, o, model, top=3)
+        plain = B.Plan(circ, bits, opts=o)
+        tree, slices = plain.tree()
+        plain.close()
+        tp, tc = [], []
+        for _ in range(3):   # alternate the two so drifts hit both
+            tp.append(_median_ms(circ, bits, tree, slices, o))
+            tc.append(_median_ms(circ, bits, ch["tree"], ch["slices"], o))
+        r = float(np.median(tc) / np.median(tp))
+        ratios.append(r)
+        print("%s: plain %.3f ms, verified choice %.3f ms (%s), ratio %.3f"
+              % (spec[:5], np.median(tp), np.median(tc), ch["source"], r))
+        plan = B.Plan(circ, bits, tree=ch["tree"], slices=ch["slices"] or None, opts=o).bind()
+        st = torch.cuda.current_stream().cuda_stream
+        hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
+        ha = torch.empty(2 * len(bits), dtype=torch.float64).pin_memory()
+        B.xeb_run(plan.handle, hb.data_ptr(), len(bits), ha.data_ptr(), st)
+        amps = ha.numpy().view(np.complex128)
+        assert rel_err(amps, statevec.amplitudes(circ, bits), circ.n_qubits).max() < 1e-5
+        plan.close()
+    gm = float(np.exp(np.mean(np.log(ratios))))
+    print("geometric mean of verified / plain: %.3f" % gm)
+    assert gm < GAIN_BOUND
