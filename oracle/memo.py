@@ -18,9 +18,11 @@ Contents
   pi's first bit most significant, so lexicographic order = numeric order; key
   ids are ranks in ascending order; the children's ids of key u are
   (uL(u), uR(u)).
-* ``alg12``: Alg. 1 driving Alg. 2 (recursive eval with a global dictionary
-  cache keyed by (subexpression; values of its variables)); returns the
-  results and the number of contractions performed per node.
+* ``alg12``: what Alg. 1 driving Alg. 2 (eval with a global cache keyed by
+  (subexpression; values of its variables)) computes, tabulated bottom-up
+  over the tree's post-order: each node contracted once per distinct value
+  of its variables among the bitstrings; returns the results and the number
+  of contractions performed per node.
 * ``alg34``: what Alg. 3 (eval_all) and Alg. 4 (eval') compute: over the
   sorted distinct tuples of leaf value indices, each node evaluated once per
   distinct sub-tuple, its right child for all distinct right parts at once
@@ -137,27 +139,43 @@ def _leaf_value_id(net: Network, j: int, word: int) -> Tuple[int, ...]:
 
 
 def alg12(net: Network, tree, bitstrings, sliced: Optional[Dict[int, int]] = None):
-    """Multi-tensor contraction with a global cache (Alg. 1) and recursive
-    eval (Alg. 2).  Returns (results in input order, contractions per node)."""
-    cache = {}
-    counts: Dict[int, int] = defaultdict(int)
+    """What Alg. 1 (the loop over bitstrings) with Alg. 2 (eval with one
+    global cache) computes, tabulated bottom-up instead of recursively: the
+    cache ends up holding one entry per node and per distinct value of the
+    variables below it (the value indices of the node's leaves) that some
+    bitstring reaches, each computed once from its children's entries.  So
+    walk the nodes in post-order (the tree's own order), and for each node
+    contract once per distinct tuple of its leaves' value indices among the
+    bitstrings.  Returns (results in input order, contractions per node)."""
+    words = [int(w) for w in np.asarray(bitstrings, dtype=np.uint64)]
     leaves_of = {i: inorder_leaves(tree, i) for i in range(len(tree))}
+    counts: Dict[int, int] = defaultdict(int)
 
-    def ev(ref, word):
+    def sub(ref, word):
+        """the tuple of leaf value indices of subtree ref for this bitstring"""
+        js = [-1 - ref] if ref < 0 else leaves_of[ref]
+        return tuple(_leaf_value_id(net, j, word) for j in js)
+
+    table: Dict[int, Dict[tuple, tuple]] = {}
+
+    def lookup(ref, word):
         if ref < 0:
             return project_leaf(net.leaves[-1 - ref], word, sliced)
-        key = (ref,) + tuple(_leaf_value_id(net, j, word) for j in leaves_of[ref])
-        if key not in cache:
-            l, r = tree[ref]
-            ul = ev(l, word)
-            ur = ev(r, word)
-            cache[key] = pair_contract(ul[0], ul[1], ur[0], ur[1])
-            counts[ref] += 1
-        return cache[key]
+        return table[ref][sub(ref, word)]
 
+    for i, (l, r) in enumerate(tree):
+        table[i] = {}
+        for w in words:
+            t = sub(i, w)
+            if t in table[i]:
+                continue
+            a, b = lookup(l, w), lookup(r, w)
+            table[i][t] = pair_contract(a[0], a[1], b[0], b[1])
+            counts[i] += 1
+    root = root_ref(tree)
     res = []
-    for w in np.asarray(bitstrings, dtype=np.uint64):
-        t, legs = ev(root_ref(tree), int(w))
+    for w in words:
+        t, legs = table[root][sub(root, w)]
         assert not legs
         res.append(complex(t))
     return np.array(res, dtype=np.complex128), dict(counts)
