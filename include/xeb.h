@@ -373,11 +373,6 @@ enum {
  * launch; host only otherwise).  Enabling resets the accumulated totals. */
 xeb_status xeb_plan_profile(struct xeb_plan_s* plan, int enable);
 
-/* Accumulated totals per kernel class since profiling was enabled: device
- * milliseconds, launches, algorithmic flops (8 per complex multiply-add) and
- * algorithmic bytes (each operand tensor read once, each result written
- * once).  Each output is a host array of XEB_N_KC doubles (may be NULL).
- * Synchronises on the recorded events. */
 /* Per contraction of the plan's program (in program order): accumulated
  * device milliseconds and launches since profiling was enabled, its kernel
  * class (XEB_KC_*, -1 before xeb_plan_bind) and its shape (M, N, K, k_v as
@@ -385,6 +380,15 @@ xeb_status xeb_plan_profile(struct xeb_plan_s* plan, int enable);
  * *n_ops receives n.  Synchronises on the recorded events. */
 xeb_status xeb_plan_profile_ops(struct xeb_plan_s* plan, int cap, double* ms, double* launches, int32_t* cls,
                                 double* shape, int32_t* n_ops);
+
+/* Kernel form of contraction step op_index of a bound plan (the fixed rule's,
+ * or the autotuner's choice after xeb_plan_autotune); host only.  Writes five
+ * values to form: [0] kernel class (XEB_KC_*); [1] rows per lane of the keyed
+ * SIMT kernel; [2] result columns per thread and [3] rows per tile of the
+ * streaming kernel; [4] 1 when the tensor-core kernel loads A with TMA boxes
+ * (entries that do not apply to the kernel are 0).  XEB_EINVAL for a NULL plan
+ * or form, an unbound plan, or an index that is not a contraction step. */
+xeb_status xeb_plan_op_form(const struct xeb_plan_s* plan, int op_index, int32_t* form);
 
 /* Work of one xeb_amplitudes step over the slices it runs (all, or the
  * subset of xeb_set_slice_subset), with cross-slice reuse: a node whose
@@ -417,6 +421,11 @@ xeb_status xeb_plan_buffers(const struct xeb_plan_s* plan, int64_t* off, int64_t
  * plan or n_out, or an index outside the program. */
 xeb_status xeb_plan_op_layout(const struct xeb_plan_s* plan, int op_index, int32_t* out, int cap, int32_t* n_out);
 
+/* Accumulated totals per kernel class since profiling was enabled: device
+ * milliseconds, launches, algorithmic flops (8 per complex multiply-add) and
+ * algorithmic bytes (each operand tensor read once, each result written
+ * once).  Each output is a host array of XEB_N_KC doubles (may be NULL).
+ * Synchronises on the recorded events. */
 xeb_status xeb_plan_profile_read(struct xeb_plan_s* plan, double* ms, double* launches, double* flops,
                                  double* bytes);
 
@@ -457,11 +466,15 @@ xeb_status xeb_mlp_train_step(struct xeb_mlp_s* mlp, const float* x_dev, const f
 
 /* Autotuner (the plan's own form of "tile shapes picked by an autotuner"):
  * runs one step to fill the operands, then for every contraction times each
- * kernel form that fits it -- tcgen05 with TMA loads, tcgen05 with gathered
- * loads, tcgen05 with W in shared memory, grouped tcgen05 (memo levels), SIMT
- * streaming -- `reps` times with CUDA events on `stream`, and keeps the
- * fastest.  Later steps use (and recapture) the chosen forms.  Synchronises
- * `stream`.  n_changed (may be NULL): contractions whose form changed. */
+ * kernel form and tile shape that fits it -- tcgen05 with TMA loads, tcgen05
+ * with gathered loads (also per key of a keyed contraction), grouped tcgen05
+ * (memo levels), deep-K tcgen05, SIMT streaming with its default tile, with
+ * two result columns per thread (a warp stores whole result rows) and with
+ * half the rows per tile, keyed SIMT with one or two rows per lane (also for
+ * single-key contractions) -- `reps` times with CUDA events on `stream`, and
+ * keeps the fastest.  Later steps use (and recapture) the chosen forms.
+ * Synchronises `stream`.  n_changed (may be NULL): contractions whose form
+ * changed. */
 xeb_status xeb_plan_autotune(struct xeb_plan_s* plan, int reps, uintptr_t stream, int32_t* n_changed);
 
 /* Linear XEB of k complex128 amplitudes already in device memory (amps_dev,

@@ -137,6 +137,7 @@ _PROTOS = {
     "xeb_plan_op_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p, ctypes.c_int, _i32p]),
     "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
                                             ctypes.POINTER(ctypes.c_int32)]),
+    "xeb_plan_op_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p]),
     "xeb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -318,6 +319,15 @@ def xeb_plan_op_layout(plan, op_index: int):
         out[name] = v[pos:pos + ln]
         pos += ln
     return out
+
+
+def xeb_plan_op_form(plan, op_index: int) -> dict:
+    """Kernel form of one contraction step: class name, keyed rows per lane,
+    streaming columns per thread and rows per tile, TMA loads."""
+    v = np.zeros(5, dtype=np.int32)
+    _check(load().xeb_plan_op_form(plan, op_index, _ptr(v, ctypes.c_int32)))
+    return {"kernel": KERNEL_CLASSES[v[0]] if 0 <= v[0] < len(KERNEL_CLASSES) else None, "rows_per_lane": int(v[1]),
+            "cols_per_thread": int(v[2]), "rows_per_tile": int(v[3]), "tma": int(v[4])}
 
 
 def xeb_plan_buffers(plan):

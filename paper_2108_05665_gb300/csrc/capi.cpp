@@ -52,9 +52,12 @@ constexpr int kSplitTermsDefault = 4;
 constexpr uint32_t kTimeoutMsDefault = 2000;
 
 // kernel-form choices of a contraction (autotuner candidates)
+// (CH_STREAM_N2 / CH_STREAM_HALF: tile shapes of the streaming kernel -- two
+// result columns per thread, so a warp stores whole result rows; half the
+// rows per tile)
 enum Choice {
     CH_AUTO = -1, CH_TC2 = 0, CH_TC2_GATHER = 1, CH_GROUPED = 2, CH_TCKD = 3, CH_SIMT = 4, CH_KEYED = 5, CH_KEYED2 = 6,
-    CH_COUNT = 7
+    CH_STREAM_N2 = 7, CH_STREAM_HALF = 8, CH_COUNT = 9
 };
 
 struct GemmLaunch {
@@ -332,15 +335,22 @@ bool encode_a_map(const xebk::TcDesc& t, const float2* arena, CUtensorMap& map) 
 
 // Tile shape of the streaming kernel for a contraction, or false if the
 // contraction does not fit it.
-bool stream_tile(const Op& op, size_t elem, xebk::StreamDesc& s) {
+// npt_force > 0: that many result columns per thread (a divisor of N);
+// half_rows: half the rows per tile the default rule picks.
+bool stream_tile(const Op& op, size_t elem, xebk::StreamDesc& s, int npt_force = 0, bool half_rows = false) {
     if (op.K > xebk::kStreamMaxK || op.N > xebk::kStreamMaxN || op.M < 64) return false;
-    const int npt = op.N <= 8 ? int(op.N) : (op.N == 16 ? 8 : 16);
+    int npt = op.N <= 8 ? int(op.N) : (op.N == 16 ? 8 : 16);
+    if (npt_force > 0) {
+        if (op.N < npt_force || op.N % npt_force != 0) return false;
+        npt = npt_force;
+    }
     const int tpr = int(op.N) >= npt ? int(op.N) / npt : 1;
     const int rg = 256 / tpr;
     int R = 1;
     while (2 * R <= op.M && 2 * R * op.K <= 256 * xebk::kStreamEPT && 2 * R <= rg * std::max(1, 16 / npt) &&
            size_t(2 * R) * size_t(op.K) * elem <= 16 * 1024)
         R *= 2;
+    if (half_rows) R /= 2;
     if (R < 32 || R * op.K > 256 * xebk::kStreamEPT) return false;
     int tm = 0;
     while ((1 << tm) < R) ++tm;
@@ -1282,11 +1292,11 @@ void layout_device(xeb_plan_s* p) {
     {   // memo-level contractions: per-group A offsets + packed B vectors (largest op)
         size_t mx = 16;
         for (const Op& op : p->prog.ops)
-            if (op.kind != OP_PERM && op.kv > 1) {
-                if (op.N == 1)
+            if (op.kind != OP_PERM && op.kv >= 1) {
+                if (op.N == 1 && op.kv > 1)
                     mx = std::max(mx, xebk::memo_scratch_bytes(std::max(an.nodes[op.a_node].kv, an.nodes[op.b_node].kv),
                                                                op.kv, op.K, p->elem));
-                if (xebk::keyed_fits(op.M, op.N, op.K))
+                if (xebk::keyed_fits(op.M, op.N, op.K))   // keyed form, single-key contractions included
                     mx = std::max(mx, xebk::keyed_scratch_bytes(an.nodes[op.b_node].kv, op.K, op.N));
             }
         p->t_memo = take(int64_t(mx));
@@ -1376,8 +1386,11 @@ std::vector<char> fold_host_data(xeb_plan_s* p) {
 // Keyed SIMT form (keyed.cu): complex64, k_v > 1 keys grouped by left key (or
 // one group), K in {4, 8, 16, 32}, N in {1, 2, 4, 8, 16}, M a multiple of 32,
 // row-major results at even float2 offsets, summed bits below address bit 31.
-bool keyed_ok(const xeb_plan_s* p, const Op& op, const xebk::GemmDesc& d) {
-    if (p->elem != 8 || op.kv <= 1 || !xebk::keyed_fits(op.M, op.N, op.K) || !d.c_natural) return false;
+// single: also contractions with one key (one left-key group; every row of
+// A multiplied by the one B)
+bool keyed_ok(const xeb_plan_s* p, const Op& op, const xebk::GemmDesc& d, bool single = false) {
+    if (p->elem != 8 || op.kv < 1 || (op.kv == 1 && !single) || !xebk::keyed_fits(op.M, op.N, op.K) || !d.c_natural)
+        return false;
     if (!d.gstart && d.n_groups != 1) return false;
     if (d.c_off % 2 != 0 || d.c_key % 2 != 0) return false;
     for (int i = 0; i < d.nak; ++i)
@@ -1451,7 +1464,11 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
     }
     // keyed contractions with few summed values and narrow results, complex64
     // (keyed.cu): the default SIMT form where it fits
-    if ((ch == CH_AUTO || ch == CH_KEYED || ch == CH_KEYED2) && keyed_ok(p, op, d)) {
+    // single-key contractions take the keyed form by default where it measured
+    // faster than the streaming kernel (30-qubit plans: K = N = 4, 8, 16; the
+    // streaming kernel stays faster for K = 4, N = 16)
+    const bool keyed_default = op.kv > 1 || op.K >= 8 || op.N <= 4;
+    if (((ch == CH_AUTO && keyed_default) || ch == CH_KEYED || ch == CH_KEYED2) && keyed_ok(p, op, d, true)) {
         const bool rows2 = xebk::keyed_fits_rows2(op.M, op.N, op.K);
         if (ch == CH_KEYED2 && !rows2) return false;
         g.kernel = xebk::GK_KEYED;
@@ -1460,9 +1477,16 @@ bool select_kernel(xeb_plan_s* p, const Op& op, int ch, GemmLaunch& g) {
         return true;
     }
     if (ch == CH_KEYED || ch == CH_KEYED2) return false;
-    if (ch != CH_AUTO && ch != CH_SIMT) return false;
-    if (stream_tile(op, p->elem, g.s))
+    const bool shape_ch = ch == CH_STREAM_N2 || ch == CH_STREAM_HALF;
+    if (ch != CH_AUTO && ch != CH_SIMT && !shape_ch) return false;
+    // few summed values and wide results: the stores dominate, so by default
+    // two result columns per thread (a warp writes whole result rows)
+    const bool wide_store = op.K <= 4 && op.N >= 32;
+    if (stream_tile(op, p->elem, g.s, ch == CH_STREAM_N2 || (ch == CH_AUTO && wide_store) ? 2 : 0,
+                    ch == CH_STREAM_HALF)) {
         g.kernel = op.N == 1 && op.kv > 1 && d.gstart ? xebk::GK_MEMO : xebk::GK_STREAM;
+        if (shape_ch && g.kernel != xebk::GK_STREAM) return false;
+    } else if (shape_ch) return false;
     // N = 1 with a deep sum over few rows: a warp per output (the GEMV kernel
     // would run one long dependent chain per thread on a nearly idle GPU)
     else if (op.N == 1 && op.K >= 128 && op.M <= 64) g.kernel = xebk::GK_TAIL;
@@ -1749,7 +1773,7 @@ bool validate_launches(const xeb_plan_s* p, std::string& why) {
         }
         if (p->gemms[i].kernel == xebk::GK_KEYED) {
             const GemmLaunch& gl = p->gemms[i];
-            if (!keyed_ok(p, op, g) || gl.kvB != kb || (kb > 1 && !g.uR) ||
+            if (!keyed_ok(p, op, g, true) || gl.kvB != kb || (kb > 1 && !g.uR) ||
                 !(gl.rpt == 1 || (gl.rpt == 2 && xebk::keyed_fits_rows2(g.M, g.N, g.K)))) {
                 why = "keyed form of node " + std::to_string(op.node);
                 return false;
@@ -2334,9 +2358,10 @@ extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t strea
         for (int ch = 0; ch < CH_COUNT && s == XEB_OK; ++ch) {
             GemmLaunch g = keep;
             if (!select_kernel(p, pr.ops[i], ch, g)) continue;
-            const std::pair<int, int> form{g.kernel, g.kernel == GK_TC2      ? g.tc.tma + 2 * g.tc.grp
-                                                     : g.kernel == xebk::GK_KEYED ? g.rpt
-                                                                                  : 0};
+            const std::pair<int, int> form{g.kernel, g.kernel == GK_TC2             ? g.tc.tma + 2 * g.tc.grp
+                                                     : g.kernel == xebk::GK_KEYED  ? g.rpt
+                                                     : g.kernel == xebk::GK_STREAM ? g.s.npt * 4096 + g.s.R
+                                                                                   : 0};
             if (std::find(seen.begin(), seen.end(), form) != seen.end()) continue;
             seen.push_back(form);
             p->gemms[i] = g;
@@ -2361,7 +2386,8 @@ extern "C" xeb_status xeb_plan_autotune(xeb_plan_s* p, int reps, uintptr_t strea
         GemmLaunch g = keep;
         select_kernel(p, pr.ops[i], best.second, g);
         const bool differs = g.kernel != keep.kernel || (g.kernel == GK_TC2 && (g.tc.tma != keep.tc.tma || g.tc.grp != keep.tc.grp)) ||
-                             (g.kernel == xebk::GK_KEYED && g.rpt != keep.rpt);
+                             (g.kernel == xebk::GK_KEYED && g.rpt != keep.rpt) ||
+                             (g.kernel == xebk::GK_STREAM && (g.s.npt != keep.s.npt || g.s.R != keep.s.R));
         p->choice[i] = best.second;
         p->gemms[i] = g;
         changed += differs;
@@ -2483,6 +2509,24 @@ extern "C" xeb_status xeb_plan_profile_ops(xeb_plan_s* p, int cap, double* ms, d
             shape[4 * i + 3] = double(op.kv);
         }
     }
+    return XEB_OK;
+}
+
+extern "C" xeb_status xeb_plan_op_form(const xeb_plan_s* p, int op_index, int32_t* form) {
+    if (!p || !form) return fail(XEB_EINVAL, "NULL plan or form");
+    if (!p->bound) return fail(XEB_EINVAL, "plan not bound to device memory (call xeb_plan_bind)");
+    if (op_index < 0 || size_t(op_index) >= p->prog.ops.size() || p->prog.ops[size_t(op_index)].kind == OP_PERM ||
+        p->gemms.size() <= size_t(op_index))
+        return fail(XEB_EINVAL, "op_index is not a contraction step of the plan");
+    static const int cls_of[8] = {XEB_KC_GEMM_GENERIC, XEB_KC_GEMM_TILED, XEB_KC_GEMM_GEMV, XEB_KC_GEMM_TAIL,
+                                  XEB_KC_GEMM_STREAM,  XEB_KC_GEMM_MEMO,  XEB_KC_GEMM_KDEEP, XEB_KC_GEMM_KEYED};
+    const GemmLaunch& g = p->gemms[size_t(op_index)];
+    const int kk = g.kernel;
+    form[0] = kk == GK_TCKD ? XEB_KC_GEMM_TC_KDEEP : kk >= GK_TC2 ? XEB_KC_GEMM_TC : cls_of[kk];
+    form[1] = kk == xebk::GK_KEYED ? g.rpt : 0;
+    form[2] = kk == xebk::GK_STREAM || kk == xebk::GK_MEMO ? g.s.npt : 0;
+    form[3] = kk == xebk::GK_STREAM || kk == xebk::GK_MEMO ? g.s.R : 0;
+    form[4] = kk == GK_TC2 ? g.tc.tma : 0;
     return XEB_OK;
 }
 

@@ -457,11 +457,16 @@ def test_new_entry_points_reject_bad_arguments(lib):
     assert B.load().xeb_plan_buffers(None, None, None, None, C.byref(n)) == 1
     assert B.load().xeb_plan_step_flops(None, None, None) == 1
     assert B.load().xeb_plan_op_layout(None, 0, None, 0, C.byref(n)) == 1
+    form = np.zeros(5, dtype=np.int32)
+    assert B.load().xeb_plan_op_form(None, 0, form.ctypes.data_as(C.POINTER(C.c_int32))) == 1
     plan = B.xeb_plan_create(circ, bits)
     try:
         assert B.load().xeb_plan_buffers(plan, None, None, None, None) == 1
         with pytest.raises(B.XebError):
             B.xeb_plan_op_layout(plan, -1)
+        with pytest.raises(B.XebError):      # not bound: no kernel forms yet
+            B.xeb_plan_op_form(plan, 0)
+        assert B.load().xeb_plan_op_form(plan, 0, None) == 1
         off, el, mk = B.xeb_plan_buffers(plan)
         assert len(off) == 2 * len(B.xeb_network_leaves(circ)[0]) - 1
         assert np.all(el > 0) and np.all(off >= 0) and np.all(mk == 0xFFFFFFFF)   # unsliced: no reuse
