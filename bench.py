@@ -288,7 +288,10 @@ def main():
     if args.planner == "learned":
         from paper_2108_05665_gb300 import costmodel
         wpath = os.path.join(os.path.dirname(os.path.abspath(costmodel.__file__)), "costmodel_weights.npz")
-        chosen = costmodel.choose_verified(circ, bits, o, costmodel.CostModel.load(wpath), top=3, reps=2)
+        # sliced workloads: every candidate is timed on the same seeded subset
+        # of args.slices slices and scaled to its full slice sum
+        chosen = costmodel.choose_verified(circ, bits, o, costmodel.CostModel.load(wpath), top=3, reps=2,
+                                           slice_count=args.slices)
     try:
         if chosen is not None:
             plan = B.Plan(circ, bits, tree=chosen["tree"], slices=chosen["slices"] or None, opts=o)
