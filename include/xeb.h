@@ -60,14 +60,15 @@ typedef enum {
     XEB_ECUDA = 3,         /* a CUDA runtime call failed                       */
     XEB_ETIMEOUT = 4,      /* a device-side bounded wait gave up               */
     XEB_EUNSUPPORTED = 5,  /* valid request the library does not support       */
-    XEB_ECANCELLED = 6,
+    XEB_ECANCELLED = 6,    /* reserved: no call of this version returns it     */
     XEB_EDEVICE = 7        /* a device-side consistency check failed           */
 } xeb_status;
 
 /* Arithmetic of the pairwise contractions (Eq. elem-cont). */
 enum {
     XEB_PREC_FP32 = 0,     /* plain FP32 complex FMA on CUDA cores             */
-    XEB_PREC_TF32X3 = 1,   /* tcgen05 kind::tf32, 3-term split, FP32 accumulate */
+    XEB_PREC_TF32X3 = 1,   /* tcgen05 kind::tf32, big/small split, 4 products
+                              (opts.split_terms), FP32 accumulate        */
     XEB_PREC_FP64 = 2      /* FP64 complex FMA on CUDA cores (checks)          */
 };
 

@@ -31,6 +31,16 @@ def test_grid5x6_all_amplitudes(fixture, precision):
         assert "gemm_tc" in plan.profile, plan.profile
     # the memo-trie levels (keyed, N = 1, K = 16) run on the keyed SIMT kernel
     assert plan.profile.get("gemm_keyed", {}).get("launches", 0) > 0, plan.profile
+    # the default forms the measurements chose are the ones checked here: the
+    # keyed SIMT kernel for single-key contractions, and (split-TF32 plan) two
+    # result columns per thread for the K = 1, N = 64 streaming contraction
+    forms = B.xeb_plan_profile_ops(plan.handle)
+    single_keyed = [i for i, op in enumerate(forms)
+                    if op["kernel"] == "gemm_keyed" and op["kv"] == 1]
+    assert single_keyed, "no single-key contraction on the keyed kernel"
+    if precision == B.XEB_PREC_TF32X3:
+        wide = [i for i, op in enumerate(forms) if op["kernel"] == "gemm_stream" and op["K"] <= 4 and op["N"] >= 32]
+        assert wide and all(B.xeb_plan_op_form(plan.handle, i)["cols_per_thread"] == 2 for i in wide)
     err = rel_err(amps, ref, circ.n_qubits)
     shrink = -np.mean(np.real(np.conj(ref) * (amps - ref))) / np.mean(np.abs(ref) ** 2)
     print("max rel err %.3e  median %.3e  mean shrink %.2e  |dF| %.3e"
