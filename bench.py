@@ -39,6 +39,15 @@ FIXTURE = os.path.join(ROOT, "tests", "golden", "grid5x6_m14_k10000.npz")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
+# workload and precision pairs whose plans met a misaligned-address fault in a
+# contraction kernel (cause not found yet); bench.py refuses them
+KNOWN_FAULTS = {
+    ("grid6x9m1_m12_k300000", "tf32x3"): "misaligned-address fault in a contraction kernel (open issue)",
+    ("grid6x9m1_m14_k1000000", "tf32x3"): "misaligned-address fault in a contraction kernel (open issue)",
+    ("grid6x9m1_m14_k1000000", "fp32"): "misaligned-address fault in a contraction kernel (open issue)",
+}
+
+
 def workload_desc(w):
     return ("%dx%d grid random circuit, %d cycles, fSim(pi/2,pi/6) + sqrt(X/Y/W); %d bitstrings "
             "(%d ideal samples + %d uniform); memoized tree over all output bits"
@@ -264,6 +273,12 @@ def main():
     build.build()
     B.load()
     w = inputs.WORKLOADS[args.workload]
+    if (w.name, args.precision) in KNOWN_FAULTS:
+        # a contraction kernel of these plans stopped with a misaligned-address
+        # fault whose cause is not found yet: refuse rather than fault the GPU
+        print("bench.py: %s with --precision %s is disabled: %s" % (w.name, args.precision, KNOWN_FAULTS[(w.name, args.precision)]),
+              file=sys.stderr)
+        sys.exit(2)
     circ = w.circuit()
     bits = load_bitstrings(w)
     prec = {"fp32": B.XEB_PREC_FP32, "tf32x3": B.XEB_PREC_TF32X3}[args.precision]
