@@ -465,6 +465,24 @@ xeb_status xeb_mlp_gradients(struct xeb_mlp_s* mlp, const float* x_dev, const fl
 xeb_status xeb_mlp_train_step(struct xeb_mlp_s* mlp, const float* x_dev, const float* t_dev, int n, float lr,
                               float* loss_dev, uintptr_t stream);   /* one Adam step; loss_dev may be NULL */
 
+/* The planner with the learned cost model (the paper's planner has no learned
+ * part; here the model re-ranks the plain planner's candidates): builds up to
+ * max_cands candidate trees and slice sets (xeb_plan_candidates, with opts),
+ * predicts their step time with `model` (xeb_mlp_forward on `stream`, the
+ * project's own inference kernels, on the candidates' XEB_N_FEATURES features
+ * rounded to float) and creates the plan of the fastest-predicted candidate,
+ * as xeb_plan_create would with that tree and slice set.  With no candidate it
+ * falls back to the plain planner (xeb_plan_create with no tree).  The
+ * candidates are not timed here: timing the best few against the plain plan
+ * is the caller's choice (the Python `costmodel.choose_verified`).
+ * *predicted_log2_ms (may be NULL) receives the model's prediction for the
+ * chosen candidate (NaN for the fallback).  XEB_EINVAL for a NULL circuit,
+ * bitstrings, model or out or max_cands < 1; errors of the calls it makes are
+ * passed on.  Allocates two small device buffers and synchronises `stream`. */
+xeb_status xeb_plan_create_learned(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                                   const xeb_plan_opts* opts, struct xeb_mlp_s* model, int max_cands,
+                                   uintptr_t stream, double* predicted_log2_ms, struct xeb_plan_s** out);
+
 /* Autotuner (the plan's own form of "tile shapes picked by an autotuner"):
  * runs one step to fill the operands, then for every contraction times each
  * kernel form and tile shape that fits it -- tcgen05 with TMA loads, tcgen05

@@ -138,6 +138,9 @@ _PROTOS = {
     "xeb_plan_profile_ops": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dblp, _dblp, _i32p, _dblp,
                                             ctypes.POINTER(ctypes.c_int32)]),
     "xeb_plan_op_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _i32p]),
+    "xeb_plan_create_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, _dblp,
+                                               ctypes.POINTER(ctypes.c_void_p)]),
     "xeb_last_error": (ctypes.c_char_p, []),
 }
 
@@ -243,6 +246,20 @@ def xeb_plan_create(circuit, bitstrings, tree: Optional[Sequence] = None, slices
         _check(load().xeb_plan_create(ctypes.byref(ca.c), _ptr(bs, ctypes.c_uint64), len(bs), tp, sp, op,
                                       ctypes.byref(out)))
     return out
+
+
+def xeb_plan_create_learned(circuit, bitstrings, mlp, opts=None, max_cands: int = 256, stream: int = 0):
+    """xeb_plan_create_learned: the plan of the candidate `mlp` (a Mlp) predicts
+    fastest; returns (plan handle, predicted log2 ms)."""
+    ca = CircuitArrays(circuit)
+    bs = np.ascontiguousarray(bitstrings, dtype=np.uint64)
+    out = ctypes.c_void_p()
+    pred = ctypes.c_double()
+    op = ctypes.byref(opts) if opts is not None else None
+    _check(load().xeb_plan_create_learned(ctypes.byref(ca.c), _ptr(bs, ctypes.c_uint64), len(bs), op, mlp.handle,
+                                          max_cands, ctypes.c_void_p(stream or None), ctypes.byref(pred),
+                                          ctypes.byref(out)))
+    return out, pred.value
 
 
 def xeb_plan_destroy(plan):
@@ -542,6 +559,18 @@ class Plan:
         self.n = circuit.n_qubits
         self.w = len(set(open_qubits)) if open_qubits is not None else 0   # 2^w amplitudes per bitstring
         self.workspace = None
+
+    @classmethod
+    def learned(cls, circuit, bitstrings, mlp, opts=None, max_cands: int = 256, stream: int = 0):
+        """The plan of the candidate the cost model `mlp` predicts fastest
+        (xeb_plan_create_learned); .predicted_log2_ms holds the prediction."""
+        self = cls.__new__(cls)
+        self.handle, self.predicted_log2_ms = xeb_plan_create_learned(circuit, bitstrings, mlp, opts, max_cands, stream)
+        self.k = len(bitstrings)
+        self.n = circuit.n_qubits
+        self.w = 0
+        self.workspace = None
+        return self
 
     def stats(self):
         return xeb_plan_stats(self.handle)

@@ -1138,6 +1138,54 @@ extern "C" xeb_status xeb_plan_candidates(const xeb_circuit* circuit, const uint
     return XEB_OK;
 }
 
+extern "C" xeb_status xeb_plan_create_learned(const xeb_circuit* circuit, const uint64_t* bitstrings, size_t k,
+                                              const xeb_plan_opts* opts, xeb_mlp_s* model, int max_cands,
+                                              uintptr_t stream, double* predicted_log2_ms, xeb_plan_s** out) {
+    if (!circuit || !bitstrings || !model || !out) return fail(XEB_EINVAL, "NULL circuit, bitstrings, model or out");
+    if (max_cands < 1) return fail(XEB_EINVAL, "max_cands < 1");
+    if (predicted_log2_ms) *predicted_log2_ms = std::nan("");
+    Network net;
+    std::string err;
+    if (!build_network(circuit, net, err)) return fail(XEB_EINVAL, err);
+    if (net.leaves.size() < 2) return fail(XEB_EUNSUPPORTED, "network with fewer than two leaves");
+    const int nn = int(net.leaves.size()) - 1;
+    std::vector<int32_t> trees(size_t(max_cands) * size_t(nn) * 2), slices(size_t(max_cands) * 30), nsl(max_cands),
+        fam(max_cands);
+    std::vector<double> feat(size_t(max_cands) * XEB_N_FEATURES);
+    int32_t n = 0;
+    xeb_status s = xeb_plan_candidates(circuit, bitstrings, k, opts, max_cands, trees.data(), slices.data(),
+                                       nsl.data(), feat.data(), fam.data(), &n);
+    if (s != XEB_OK) return s;
+    if (n == 0) return xeb_plan_create(circuit, bitstrings, k, nullptr, nullptr, opts, out);
+    // predictions of log2 ms on the device
+    std::vector<float> xf(static_cast<size_t>(n) * XEB_N_FEATURES), yf(static_cast<size_t>(n));
+    for (size_t i = 0; i < xf.size(); ++i) xf[i] = float(feat[i]);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    float* xd = nullptr;
+    float* yd = nullptr;
+    cudaError_t e = cudaMalloc(&xd, xf.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&yd, yf.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(xd, xf.data(), xf.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        s = xeb_mlp_forward(model, xd, n, yd, stream);
+        if (s == XEB_OK) {
+            e = cudaMemcpyAsync(yf.data(), yd, yf.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+    }
+    if (xd) cudaFree(xd);
+    if (yd) cudaFree(yd);
+    if (s != XEB_OK) return s;
+    if (e != cudaSuccess) return fail(XEB_ECUDA, std::string("learned planner: ") + cudaGetErrorString(e));
+    int best = 0;
+    for (int i = 1; i < n; ++i)
+        if (yf[size_t(i)] < yf[size_t(best)]) best = i;
+    if (predicted_log2_ms) *predicted_log2_ms = double(yf[size_t(best)]);
+    const xeb_tree tree{nn, trees.data() + size_t(best) * size_t(nn) * 2};
+    const xeb_slices sl{nsl[size_t(best)], slices.data() + size_t(best) * 30};
+    return xeb_plan_create(circuit, bitstrings, k, &tree, nsl[size_t(best)] > 0 ? &sl : nullptr, opts, out);
+}
+
 extern "C" void xeb_plan_destroy(xeb_plan_s* p) {
     if (!p) return;
     drop_graph(p, p->graph_plain);

@@ -459,6 +459,8 @@ def test_new_entry_points_reject_bad_arguments(lib):
     assert B.load().xeb_plan_op_layout(None, 0, None, 0, C.byref(n)) == 1
     form = np.zeros(5, dtype=np.int32)
     assert B.load().xeb_plan_op_form(None, 0, form.ctypes.data_as(C.POINTER(C.c_int32))) == 1
+    out = C.c_void_p()
+    assert B.load().xeb_plan_create_learned(None, None, 0, None, None, 1, None, None, C.byref(out)) == 1
     plan = B.xeb_plan_create(circ, bits)
     try:
         assert B.load().xeb_plan_buffers(plan, None, None, None, None) == 1

@@ -155,3 +155,32 @@ def test_learned_planner_gains_on_held_out_circuits():
     gm = float(np.exp(np.mean(np.log(ratios))))
     print("geometric mean of verified / plain: %.3f" % gm)
     assert gm < GAIN_BOUND
+
+
+def test_learned_planner_through_the_c_abi():
+    """xeb_plan_create_learned ranks the planner's candidates with the model on
+    the device and creates the fastest-predicted one: the same tree, slices and
+    prediction as costmodel.choose with the same model, and its amplitudes
+    match the oracle."""
+    import os
+    import torch
+    from paper_2108_05665_gb300 import costmodel, train_costmodel
+    from oracle import statevec
+    from gpu_util import rel_err
+    w = os.path.join(os.path.dirname(costmodel.__file__), "costmodel_weights.npz")
+    model = costmodel.CostModel.load(w)
+    circ, bits, o = train_costmodel.make(train_costmodel.circuit_spec(HELD_OUT[1], 5000))
+    ch = costmodel.choose(circ, bits, o, model)
+    st = torch.cuda.current_stream().cuda_stream
+    plan = B.Plan.learned(circ, bits, model.mlp, o, stream=st)
+    tree, slices = plan.tree()
+    assert [tuple(t) for t in tree] == [tuple(t) for t in ch["tree"]]
+    assert sorted(slices) == sorted(ch["slices"])
+    assert abs(plan.predicted_log2_ms - ch["predicted_log2_ms"]) < 1e-6
+    plan.bind()
+    hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
+    ha = torch.empty(2 * len(bits), dtype=torch.float64).pin_memory()
+    B.xeb_run(plan.handle, hb.data_ptr(), len(bits), ha.data_ptr(), st)
+    amps = ha.numpy().view(np.complex128)
+    assert rel_err(amps, statevec.amplitudes(circ, bits), circ.n_qubits).max() < 1e-5
+    plan.close()
