@@ -556,23 +556,58 @@ __global__ void __launch_bounds__(kThreads, 1)
             // released for the next tile's MMAs once the last load has landed
             const uint32_t db = tmem + 256;
             constexpr int kMyRows = kRows / kShares;
-            for (int r0 = half * kMyRows; r0 < (half + 1) * kMyRows; r0 += 32) {
+            // staging slots of a 32-row chunk of this thread's column
+            auto stage = [&](int r0, const float* x) {
                 const int cb = S->rhi[r0 >> 5] ^ npx;
-                float v[32], w[32];
-                tm_ld32(db + lanes + uint32_t(r0), v);
-                tm_ld32(db + lanes + kRows + uint32_t(r0), w);
-                tm_wait_ld();
-                if (r0 == (half + 1) * kMyRows - 32 && !switch_w) {
-                    fence_before();
-                    bar_arrive(&S->tempty[b]);
-                }
 #pragma unroll
                 for (int i = 0; i < 32; i += 4) {
                     const int4 ro = *reinterpret_cast<const int4*>(&S->rlo[i]);
-                    cst[ro.x ^ cb] = v[i] + w[i];
-                    cst[ro.y ^ cb] = v[i + 1] + w[i + 1];
-                    cst[ro.z ^ cb] = v[i + 2] + w[i + 2];
-                    cst[ro.w ^ cb] = v[i + 3] + w[i + 3];
+                    cst[ro.x ^ cb] = x[i];
+                    cst[ro.y ^ cb] = x[i + 1];
+                    cst[ro.z ^ cb] = x[i + 2];
+                    cst[ro.w ^ cb] = x[i + 3];
+                }
+            };
+            if constexpr (kMyRows == 64) {
+                // both 32-row chunks of this warp are read and summed first, so
+                // the accumulators go back to the MMAs before any staging write
+                const int r0 = half * kMyRows;
+                float v0[32], v1[32], w[16];
+                tm_ld32(db + lanes + uint32_t(r0), v0);
+                tm_ld32(db + lanes + uint32_t(r0 + 32), v1);
+#pragma unroll
+                for (int h = 0; h < 64; h += 16) {   // the cross-term accumulator, 16 columns at a time
+                    tm_ld16(db + lanes + kRows + uint32_t(r0 + h), w);
+                    tm_wait_ld();
+                    if (h == 48 && !switch_w) {
+                        fence_before();
+                        bar_arrive(&S->tempty[b]);
+                    }
+                    float* x = h < 32 ? v0 + h : v1 + (h - 32);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) x[i] += w[i];
+                }
+                stage(r0, v0);
+                stage(r0 + 32, v1);
+            } else {
+                for (int r0 = half * kMyRows; r0 < (half + 1) * kMyRows; r0 += 32) {
+                    float v[32], w[32];
+                    tm_ld32(db + lanes + uint32_t(r0), v);
+                    tm_ld32(db + lanes + kRows + uint32_t(r0), w);
+                    tm_wait_ld();
+                    if (r0 == (half + 1) * kMyRows - 32 && !switch_w) {
+                        fence_before();
+                        bar_arrive(&S->tempty[b]);
+                    }
+                    const int cb = S->rhi[r0 >> 5] ^ npx;
+#pragma unroll
+                    for (int i = 0; i < 32; i += 4) {
+                        const int4 ro = *reinterpret_cast<const int4*>(&S->rlo[i]);
+                        cst[ro.x ^ cb] = v[i] + w[i];
+                        cst[ro.y ^ cb] = v[i + 1] + w[i + 1];
+                        cst[ro.z ^ cb] = v[i + 2] + w[i + 2];
+                        cst[ro.w ^ cb] = v[i + 3] + w[i + 3];
+                    }
                 }
             }
             if (switch_w) {

@@ -84,18 +84,6 @@ __device__ __forceinline__ int64_t scat(int64_t x, const int8_t* pos, int n) {
 // swizzled byte offset of 16-byte unit u of 128-byte row r (1024-byte atoms)
 __device__ __forceinline__ uint32_t kd_unit(int r, int u) { return uint32_t(r * 128 + ((u ^ (r & 7)) << 4)); }
 
-// 32 lanes x 16 columns of tensor memory into registers (no wait)
-__device__ __forceinline__ void tm_ld16(uint32_t ta, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(ta));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // registers into 32 lanes x 16 columns of tensor memory (no wait)
 __device__ __forceinline__ void tm_st16(uint32_t ta, const float* v) {
     asm volatile(
