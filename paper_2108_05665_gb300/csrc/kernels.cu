@@ -1216,8 +1216,61 @@ cudaError_t launch_gemm_memo(const GemmDesc& g, const StreamDesc& s, T* arena, c
     return cudaGetLastError();
 }
 
+// ---- outer products: K = 1, one key, natural layouts ------------------------------
+// C[m][n] = A[m] B[n] (the summed index is empty): all of the work is writing
+// C.  Thread t owns the column pair p = t mod (N / 2) on every row it visits,
+// keeps B[2p] and B[2p + 1] in registers and writes the two results of a row
+// as one vector store, so a warp writes whole rows (512 contiguous bytes for
+// N = 64 complex64); the lanes of a row read its A value as one broadcast.
+// Four rows per thread are loaded before any is stored.
+template <typename T>
+__global__ void __launch_bounds__(256) k_outer(const __grid_constant__ GemmDesc g, T* __restrict__ arena) {
+    const int P = int(g.N >> 1);   // column pairs per row, a power of two dividing 256
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int p = int(tid & (P - 1));
+    const int64_t ua = g.uL ? g.uL[0] : 0, ub = g.uR ? g.uR[0] : 0;
+    const T* __restrict__ A = arena + g.a_off + ua * g.a_key;
+    const T* __restrict__ B = arena + g.b_off + ub * g.b_key;
+    T* __restrict__ C = arena + g.c_off;
+    const T b0 = B[2 * p], b1 = B[2 * p + 1];
+    const int64_t rs = int64_t(gridDim.x) * blockDim.x / P;   // rows per pass of the grid
+    constexpr int U = 4;
+    for (int64_t r0 = tid / P; r0 < g.M; r0 += U * rs) {
+        T a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = r0 + u * rs < g.M ? A[r0 + u * rs] : czero<T>();
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = r0 + u * rs;
+            if (r < g.M) {
+                const T v[2] = {cfma(czero<T>(), a[u], b0), cfma(czero<T>(), a[u], b1)};
+                store_vec<2>(C + r * g.N + 2 * p, v);
+            }
+        }
+    }
+}
+
+// the outer-product kernel applies: K = 1, one key, A's rows and B's columns
+// at consecutive addresses from bit 0, C row-major, N = 2 .. 512 a power of
+// two, and 16-byte aligned result pairs and B pairs
+template <typename T>
+bool outer_fits(const GemmDesc& g) {
+    if (g.K != 1 || g.kv != 1 || g.n_groups != 1 || !g.c_natural || g.nak != 0 || g.nbk != 0) return false;
+    if (g.N < 2 || g.N > 512 || (g.N & (g.N - 1)) != 0 || g.M != (int64_t(1) << g.nam) || g.N != (int64_t(1) << g.nbn))
+        return false;
+    for (int i = 0; i < g.nam; ++i)
+        if (g.apm[i] != i) return false;
+    for (int i = 0; i < g.nbn; ++i)
+        if (g.bpn[i] != i) return false;
+    return sizeof(T) == 16 || (g.c_off % 2 == 0 && g.b_off % 2 == 0 && g.b_key % 2 == 0);
+}
+
 template <typename T>
 cudaError_t launch_gemm_stream(const GemmDesc& g, const StreamDesc& s, T* arena, cudaStream_t st) {
+    if (outer_fits<T>(g)) {
+        k_outer<T><<<152 * 8, 256, 0, st>>>(g, arena);
+        return cudaGetLastError();
+    }
     const size_t a_sz = (size_t(g.K) * (s.R + 1) + 1) & ~size_t(1);
     const size_t b_sz = g.N == 1 ? size_t(kStreamBKeys) : size_t(g.K) * (g.N + 2);
     const size_t smem = sizeof(T) * (kStreamStages * a_sz + b_sz);
