@@ -25,14 +25,15 @@
 //
 // W^T (big and small, <= 128 x 128 floats each) is written once per CTA into
 // tensor memory and serves as the MMA's A operand; the state rows are the
-// shared-memory B operand (K-major, 128-byte swizzle), so shared memory holds
-// only a ring of split state chunks.  Eight producer warps gather state
-// elements (the k legs of a contraction sit at arbitrary address bits) with
-// the loads of four chunks in flight per thread in registers, and write each
-// chunk split into big/small into its ring stage.  One thread issues the
-// MMAs; four epilogue warps
-// read D^T from tensor memory (lane = output column), transpose it through a
-// padded shared buffer and write whole rows of C.
+// shared-memory B operand (K-major, 128-byte swizzle).  Gather mode: eight
+// producer warps gather state elements (the k legs of a contraction sit at
+// arbitrary address bits) with the loads of four chunks in flight per thread
+// in registers, and write each chunk split into big/small into a ring stage.
+// TMA mode (A row-major): one thread loads whole tiles with TMA boxes and four
+// warps split them in place.  One thread issues the MMAs; the epilogue warps
+// read D^T from tensor memory (lane = output column), release it to the next
+// tile's MMAs, transpose the tile through an XOR-swizzled shared buffer and
+// write C.
 //
 // Tensor memory: columns [0, 128) W^T big, [128, 256) W^T small, [256, 384)
 // big*big accumulator, [384, 512) cross-term accumulator (128-row tiles: one
