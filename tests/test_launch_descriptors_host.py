@@ -16,8 +16,9 @@ subset of slices; every logged launch is then checked:
   (tables) or 256-byte (scratch) aligned;
 * the keyed kernel's row count a multiple of its rows per item.
 
-The 53-qubit plan with 300,000 bitstrings is the workload whose first step
-met a misaligned-address fault on the GPU.
+The 53-qubit plans with 300,000 (TF32 split) and 1,000,000 (FP32)
+bitstrings are workloads whose first step met a misaligned-address fault on
+the GPU.
 """
 import ctypes
 import os
@@ -162,7 +163,8 @@ def _check_launches(launches, arena, device):
     return gemms, problems
 
 
-@pytest.mark.parametrize("name,prec", [("grid5x6_m14_k10000", "tf32x3"), ("grid6x9m1_m12_k300000", "tf32x3")])
+@pytest.mark.parametrize("name,prec", [("grid5x6_m14_k10000", "tf32x3"), ("grid6x9m1_m12_k300000", "tf32x3"),
+                                       ("grid6x9m1_m14_k1000000", "fp32")])
 def test_launch_descriptors_are_in_range_and_aligned(emu_lib, tmp_path, name, prec):
     launches, arena, device = _emulate(emu_lib, tmp_path, name, prec)
     gemms, problems = _check_launches(launches, arena, device)
