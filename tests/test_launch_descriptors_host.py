@@ -174,6 +174,19 @@ def test_launch_descriptors_are_in_range_and_aligned(emu_lib, tmp_path, name, pr
         # the unsliced 30-qubit plan runs its sweep on the TMA tensor-core form
         assert sum(1 for d in launches if d["kind"] == "tc2" and d["tma"]) >= 20
         assert sum(1 for d in launches if d["kind"] == "tmap") >= 20
+        # and its large K = 1 outer product (2^24 x 64 results) meets the
+        # outer-product kernel's conditions (natural layouts, even offsets)
+        outer = [d for d in launches if d["kind"] == "stream" and _outer_fits(d)]
+        assert any(d["M"] == 1 << 24 and d["N"] == 64 for d in outer)
+
+
+def _outer_fits(d):
+    """The conditions under which the streaming launcher runs k_outer."""
+    M, N = d["M"], d["N"]
+    return (d["K"] == 1 and d["kv"] == 1 and d["n_groups"] == 1 and d["c_natural"] and d["nak"] == 0
+            and d["nbk"] == 0 and 2 <= N <= 512 and N & (N - 1) == 0 and M == 1 << d["nam"] and N == 1 << d["nbn"]
+            and d["apm"] == list(range(d["nam"])) and d["bpn"] == list(range(d["nbn"]))
+            and d["c_off"] % 2 == 0 and d["b_off"] % 2 == 0 and d["b_key"] % 2 == 0)
 
 
 def test_stub_helpers_match_the_library(emu_lib):
